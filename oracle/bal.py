@@ -1,0 +1,221 @@
+"""Algorithm 1 (barrier-augmented Lagrangian) with exact linear solves: the
+FP64 reference time step (test infrastructure).
+
+One backward-Euler step (Sec. 3.1) minimises L_sigma by the primal-dual loop
+of Algorithm 1 (Sec. 3.3) with the schedule of Sec. 3.4. Readings of the
+paper used here (each one is recorded in the design notes):
+
+* one loop iteration l = one inexact Newton step (assemble, solve, line
+  search) followed by the dual update; the convergence test uses
+  e = grad L at x^[l] and, when it passes, x^[l] is returned;
+* "min d^[l+1]" in the A' rule is the minimum distance over A at the current
+  iterate, compared with the value of the previous iteration (min of the
+  empty set = +inf);
+* A' rebuilds keep mu for pairs that stay in A'; dropped pairs lose it;
+* s_i = max(-mu_i/sigma - dhat + d_i, 0) is evaluated at the start of an
+  iteration and held fixed inside it; the dual update re-evaluates it at the
+  new iterate before mu_i += sigma b(d_i, dhat + s_i);
+* sigma update: sigma <- min(1.2 sigma, 100 sigma0) (the printed max(...) is
+  read as a cap; the literal form is available as `sigma_literal_max`);
+* sigma0 = -(sum grad b)^T grad E / ||sum grad b||^2 over A at x_0 (the
+  printed denominator is not squared, which is not dimensionally
+  consistent), floored at mbar / (h^2 b''(dhat/2, dhat));
+* line search: alpha_0 = min(1, min over pairs of 0.9 d_i / Delta_i) where
+  Delta_i bounds how fast the pair can close along p; halve until no tet is
+  inverted, the number of active pairs is within the memory cap (Sec. 5.2),
+  and L_sigma does not increase by more than a rounding slack.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from . import barrier, contact, elastic
+from .system import PairSet, energy_parts, gradient, hessian, inertia_target
+
+
+@dataclasses.dataclass
+class Params:
+    newton_tol: float = 1e-4        # ||e^l|| / ||e^0|| (Alg. 1)
+    newton_abs_tol: float = 0.0
+    newton_max: int = 200
+    ap_ratio: float = 1e-2          # A' threshold 1e-2 dhat (Alg. 1)
+    sigma_growth: float = 1.2
+    sigma_cap: float = 100.0
+    sigma_literal_max: bool = False
+    step_bound: float = 0.9
+    ls_min_alpha: float = 1e-9      # App. B
+    ls_slack: float = 1e-12
+    contact_cap: int = 1 << 30      # Sec. 5.2 memory limit on |A|
+
+
+def sigma_floor(model):
+    b2 = float(barrier.d2b(np.array([model.dhat / 2]), model.dhat)[0])
+    return float(np.mean(model.mass)) / (model.h ** 2 * b2)
+
+
+def active_pairs(model, x):
+    """A at x: pairs with d < dhat (sorted keys) and their distances."""
+    cand = contact.candidate_pairs(x, model.scene, model.dhat)
+    if not cand:
+        return [], np.zeros(0)
+    d, _, _ = contact.pair_distances(x, cand, model.scene)
+    keep = d < model.dhat
+    return [k for k, m in zip(cand, keep) if m], d[keep]
+
+
+def initial_sigma(model, x, y, A_keys):
+    floor = sigma_floor(model)
+    if not A_keys:
+        return floor
+    n = len(A_keys)
+    ps = PairSet(A_keys, np.ones(n, bool), np.zeros(n, bool), np.zeros(n), np.zeros(n))
+    _, gE, gb = gradient(model, x, y, ps, 1.0, parts=True)
+    nb2 = float(np.sum(gb * gb))
+    if nb2 <= 0.0:
+        return floor
+    return max(-float(np.sum(gb * gE)) / nb2, floor)
+
+
+def make_pairset(model, x, A_keys, Ap, sigma):
+    keys = sorted(set(A_keys) | set(Ap))
+    if not keys:
+        return PairSet([], np.zeros(0, bool), np.zeros(0, bool), np.zeros(0), np.zeros(0))
+    Aset = set(A_keys)
+    inA = np.array([k in Aset for k in keys])
+    inAp = np.array([k in Ap for k in keys])
+    mu = np.array([Ap.get(k, 0.0) for k in keys])
+    d, _, _ = contact.pair_distances(x, keys, model.scene)
+    s = np.where(inAp, np.maximum(-mu / sigma - model.dhat + d, 0.0), 0.0)
+    return PairSet(keys, inA, inAp, mu, s)
+
+
+def displacement_bound(pairs, p_norm, scene):
+    """Delta_i = max node speed on the first primitive + on the second."""
+    nodes = contact.stencil_nodes(pairs, scene)
+    pn = p_norm[nodes]
+    is_pt = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)[:, 0] == 0
+    return np.where(is_pt, pn[:, 0] + pn[:, 1:].max(axis=1),
+                    pn[:, :2].max(axis=1) + pn[:, 2:].max(axis=1))
+
+
+def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
+    sc = model.scene
+    pnorm = np.sqrt(np.sum(p * p, axis=1))
+    delta = float(pnorm[sc.surf_verts].max()) if sc.surf_verts.size else 0.0
+    r = model.dhat + 2.0 * delta / prm.step_bound
+    cand = contact.candidate_pairs(x, sc, r)
+    alpha = 1.0
+    if cand:
+        d0, _, _ = contact.pair_distances(x, cand, sc)
+        Dl = displacement_bound(cand, pnorm, sc)
+        m = prm.step_bound * d0 < Dl
+        if np.any(m):
+            alpha = min(1.0, float(np.min(prm.step_bound * d0[m] / Dl[m])))
+    parts_old = energy_parts(model, x, y, ps, sigma)
+    E_old = sum(parts_old)
+    slack = prm.ls_slack * sum(abs(t) for t in parts_old)
+    Ap_idx = [i for i, f in enumerate(ps.inAp) if f]
+    Ap_keys = {ps.keys[i]: (ps.mu[i], ps.s[i]) for i in Ap_idx}
+    trials = 0
+    while alpha >= prm.ls_min_alpha:
+        trials += 1
+        xn = x + alpha * p
+        F = elastic.deformation_gradient(xn, sc.tets, model.Dm_inv)
+        if np.any(np.linalg.det(F) <= 0):
+            alpha *= 0.5
+            continue
+        if cand:
+            dn, _, _ = contact.pair_distances(xn, cand, sc)
+            A_new = [k for k, dd in zip(cand, dn) if dd < model.dhat]
+        else:
+            A_new = []
+        if len(A_new) > prm.contact_cap:
+            alpha *= 0.5
+            continue
+        keys = sorted(set(A_new) | set(Ap_keys))
+        Aset = set(A_new)
+        psn = PairSet(keys, np.array([k in Aset for k in keys], dtype=bool),
+                      np.array([k in Ap_keys for k in keys], dtype=bool),
+                      np.array([Ap_keys.get(k, (0.0, 0.0))[0] for k in keys]),
+                      np.array([Ap_keys.get(k, (0.0, 0.0))[1] for k in keys]))
+        E_new = sum(energy_parts(model, xn, y, psn, sigma))
+        if E_new - E_old <= slack:
+            return alpha, xn, dict(trials=trials, E_old=E_old, E_new=E_new,
+                                   n_cand=len(cand))
+        alpha *= 0.5
+    return 0.0, x, dict(trials=trials, E_old=E_old, failed=True, n_cand=len(cand))
+
+
+def solve(H, rhs):
+    n = H.shape[0]
+    if n <= 12000:
+        c = sla.cho_factor(H.toarray(), lower=True)
+        return sla.cho_solve(c, rhs)
+    return spla.splu(H.tocsc()).solve(rhs)
+
+
+def time_step(model, x_t, v_t, prm: Params = Params(), log=None):
+    """One BAL time step from (x_t, v_t). Returns (x_{t+1}, v_{t+1}, info)."""
+    dh = model.dhat
+    y = inertia_target(model, x_t, v_t)
+    x = np.array(x_t, dtype=np.float64, copy=True)
+    A_keys, A_d = active_pairs(model, x)
+    sigma0 = initial_sigma(model, x, y, A_keys)
+    sigma = sigma0
+    Ap = {}
+    dmin_prev = math.inf
+    info = dict(sigma0=sigma0, iters=0, converged=False, ls_failed=False, log=[])
+    e0 = None
+    for l in range(prm.newton_max):
+        if l > 0:
+            A_keys, A_d = active_pairs(model, x)
+        dmin = float(A_d.min()) if A_d.size else math.inf
+        if l > 0:
+            # dual update of the previous iteration, evaluated at x^[l]
+            if Ap:
+                keys = sorted(Ap)
+                d_ap, _, _ = contact.pair_distances(x, keys, model.scene)
+                for k, dd in zip(keys, d_ap):
+                    mu = Ap[k]
+                    s = max(-mu / sigma - dh + dd, 0.0)
+                    Ap[k] = mu + sigma * float(barrier.b(np.array([dd]), dh + s)[0])
+            if dmin < prm.ap_ratio * dh:
+                if prm.sigma_literal_max:
+                    sigma = max(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
+                else:
+                    sigma = min(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
+        # augmentation set rule (Alg. 1 lines 3-6)
+        if dmin > prm.ap_ratio * dh:
+            Ap = {}
+        elif dmin < dmin_prev or not Ap:
+            Ap = {k: Ap.get(k, 0.0) for k, dd in zip(A_keys, A_d) if dd < prm.ap_ratio * dh}
+        dmin_prev = dmin
+        ps = make_pairset(model, x, A_keys, Ap, sigma)
+        e = gradient(model, x, y, ps, sigma)
+        en = float(np.linalg.norm(e))
+        rec = dict(l=l, nA=len(A_keys), nAp=len(Ap), sigma=sigma, dmin=dmin, enorm=en)
+        info["log"].append(rec)
+        if e0 is None:
+            e0 = en
+        if en <= prm.newton_abs_tol or (l > 0 and en <= prm.newton_tol * e0):
+            info["converged"] = True
+            break
+        H = hessian(model, x, y, ps, sigma)
+        p = solve(H, -e.ravel()).reshape(-1, 3)
+        alpha, xn, lsi = line_search(model, x, y, p, ps, sigma, prm)
+        rec["alpha"] = alpha
+        rec["ls_trials"] = lsi["trials"]
+        info["iters"] = l + 1
+        if lsi.get("failed"):
+            info["ls_failed"] = True
+            break
+        x = xn
+    info["sigma"] = sigma
+    info["Ap"] = dict(Ap)
+    v = (x - x_t) / model.h
+    if log is not None:
+        log.append(info)
+    return x, v, info

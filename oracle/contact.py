@@ -1,0 +1,124 @@
+"""Contact pairs and their barrier / augmented-Lagrangian terms, FP64
+(test infrastructure).
+
+Constraint set (Sec. 3.1, Eq. problem): every point-triangle pair (surface
+vertex v, surface triangle t, v not a vertex of t) and every edge-edge pair
+(surface edges e < f sharing no vertex) whose unsigned distance is below the
+offset dhat is active (the set A). Pairs are identified by
+(kind, first id, second id) with kind 0 = PT (vertex id, triangle index) and
+kind 1 = EE (edge index, edge index).
+
+Per pair i the energy of Eq. (aug-lag) is a function of d_i only:
+
+    phi_i(d) = [i in A] sigma b(d, dhat)
+             + [i in A'] ( mu_i (dhat + s_i - d) + sigma b(d, dhat + s_i) ),
+
+so grad = phi' grad d and Hessian = phi'' grad d grad d^T + phi' Hess d; the
+12x12 stencil Hessian is then projected to the nearest PSD matrix
+(Sec. 4.2.2). s_i (Sec. 3.2.2) is held fixed inside an iteration.
+"""
+import numpy as np
+from scipy.spatial import cKDTree
+
+from . import barrier, distance
+from .elastic import project_psd
+
+
+def _pt_candidates(x, surf_verts, tris, r):
+    P = x[surf_verts]
+    T = x[tris]
+    c = T.mean(axis=1)
+    rad = np.sqrt(((T - c[:, None, :]) ** 2).sum(-1)).max(axis=1)
+    tree_t = cKDTree(c)
+    tree_p = cKDTree(P)
+    sm = tree_p.sparse_distance_matrix(tree_t, r + rad.max() + 1e-15, output_type="ndarray")
+    if sm.size == 0:
+        return []
+    iv, it = sm["i"].astype(np.int64), sm["j"].astype(np.int64)
+    keep = sm["v"] <= r + rad[it] + 1e-15
+    iv, it = iv[keep], it[keep]
+    v = surf_verts[iv].astype(np.int64)
+    keep = ~np.any(tris[it] == v[:, None], axis=1)
+    return list(zip([0] * int(keep.sum()), v[keep].tolist(), it[keep].tolist()))
+
+
+def _ee_candidates(x, edges, r):
+    S = x[edges]
+    c = S.mean(axis=1)
+    rad = 0.5 * np.sqrt(((S[:, 1] - S[:, 0]) ** 2).sum(-1))
+    tree = cKDTree(c)
+    pairs = tree.query_pairs(r + 2 * rad.max() + 1e-15, output_type="ndarray")
+    if pairs.size == 0:
+        return []
+    e, f = pairs.min(axis=1), pairs.max(axis=1)
+    keep = np.sqrt(((c[e] - c[f]) ** 2).sum(-1)) <= r + rad[e] + rad[f] + 1e-15
+    e, f = e[keep], f[keep]
+    share = np.any(edges[e][:, :, None] == edges[f][:, None, :], axis=(1, 2))
+    e, f = e[~share], f[~share]
+    return [(1, int(a), int(b)) for a, b in zip(e, f)]
+
+
+def candidate_pairs(x, scene, r):
+    """All PT / EE pairs whose primitives' bounding spheres come within r of
+    each other (a superset of the pairs with d < r), sorted by key."""
+    pairs = _pt_candidates(x, scene.surf_verts, scene.tris, r) + \
+        _ee_candidates(x, scene.edges, r)
+    pairs.sort()
+    return pairs
+
+
+def stencil_nodes(pairs, scene):
+    """[n,4] vertex ids of each pair's stencil."""
+    if not len(pairs):
+        return np.zeros((0, 4), dtype=np.int64)
+    P = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)
+    out = np.zeros((P.shape[0], 4), dtype=np.int64)
+    pt = P[:, 0] == 0
+    out[pt, 0] = P[pt, 1]
+    out[pt, 1:] = scene.tris[P[pt, 2]]
+    ee = ~pt
+    out[ee, :2] = scene.edges[P[ee, 1]]
+    out[ee, 2:] = scene.edges[P[ee, 2]]
+    return out
+
+
+def pair_distances(x, pairs, scene):
+    """Unsigned distance and region of every pair at x."""
+    if not pairs:
+        return np.zeros(0), [], np.zeros((0, 4), dtype=np.int64)
+    nodes = stencil_nodes(pairs, scene)
+    X4 = x[nodes]
+    is_ee = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)[:, 0] == 1
+    regions = distance.classify(X4, is_ee)
+    return distance.distances(X4, regions), regions, nodes
+
+
+def phi_derivs(d, inA, inAp, mu, s, sigma, dhat):
+    """phi, phi', phi'' of the per-pair energy (vectorised over pairs)."""
+    inA = np.asarray(inA, dtype=np.float64)
+    inAp = np.asarray(inAp, dtype=np.float64)
+    c2 = dhat + np.asarray(s, dtype=np.float64)
+    e = inA * sigma * barrier.b(d, dhat) + inAp * (mu * (c2 - d) + sigma * barrier.b(d, c2))
+    e1 = inA * sigma * barrier.db(d, dhat) + inAp * (-mu + sigma * barrier.db(d, c2))
+    e2 = inA * sigma * barrier.d2b(d, dhat) + inAp * sigma * barrier.d2b(d, c2)
+    return e, e1, e2
+
+
+def contact_terms(x, pairs, scene, inA, inAp, mu, s, sigma, dhat, project=True):
+    """Per-pair energy [n], gradient [n,12], Hessian [n,12,12] (projected),
+    stencil nodes [n,4] and distances [n]."""
+    n = len(pairs)
+    if n == 0:
+        return (np.zeros(0), np.zeros((0, 12)), np.zeros((0, 12, 12)),
+                np.zeros((0, 4), dtype=np.int64), np.zeros(0))
+    nodes = stencil_nodes(pairs, scene)
+    X4 = x[nodes]
+    is_ee = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)[:, 0] == 1
+    regions = distance.classify(X4, is_ee)
+    d, gd, Hd = distance.distance_derivatives(X4, regions)
+    e, e1, e2 = phi_derivs(d, inA, inAp, mu, s, sigma, dhat)
+    g = e1[:, None] * gd
+    H = e2[:, None, None] * gd[:, :, None] * gd[:, None, :] + e1[:, None, None] * Hd
+    if project:
+        H = project_psd(H)
+    return e, g, H, nodes, d
