@@ -1,0 +1,230 @@
+/*
+ * libbal -- C ABI of the barrier-augmented Lagrangian (BAL) inexact Newton-PCG
+ * time step of "Barrier-Augmented Lagrangian for GPU-based Elastodynamic
+ * Contact" (arXiv 2407.00046), hand-written CUDA for sm_103a (B300).
+ *
+ * Conventions shared by every entry point
+ *   - Positions, velocities and gradients are FP64 arrays [n_verts][3]
+ *     (x0 y0 z0 x1 y1 z1 ...), row-major, in DEVICE memory owned by the caller,
+ *     unless a parameter says "host".
+ *   - Every call that launches work takes a cudaStream_t (passed as void*, NULL
+ *     = legacy default stream); all work of the call is ordered on that stream.
+ *     Calls that return host-visible results (counts, norms, decisions)
+ *     synchronise that stream before returning.
+ *   - Errors are returned as bal_status, never thrown, printed or trapped. A
+ *     non-OK status leaves the scene usable; bal_last_error() returns a message
+ *     describing the calling thread's last failure.
+ *   - A bal_scene is not thread-safe: one call at a time per scene.
+ */
+#ifndef BAL_H_
+#define BAL_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BAL_OK = 0,
+  BAL_ERR_ARG = 1,            /* invalid argument / size / pointer */
+  BAL_ERR_CAPACITY = 2,       /* a contact buffer exceeded its hard limit */
+  BAL_ERR_NOT_CONVERGED = 3,  /* Newton loop hit newton_max_iter */
+  BAL_ERR_NAN = 4,            /* NaN / Inf in a gradient, residual or energy */
+  BAL_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  BAL_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  BAL_ERR_LINE_SEARCH = 7,    /* step length fell below ls_min_alpha */
+  BAL_ERR_STATE = 8           /* call order violated (e.g. solve before assemble) */
+} bal_status;
+
+typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1 } bal_precision;
+typedef enum { BAL_PRECOND_BJ = 0, BAL_PRECOND_BJ_WARMSTART = 1 } bal_precond;
+
+/* Solver and schedule parameters. bal_default_params follows the paper: Newton
+ * tolerance 1e-4 relative (Alg. 1 / Sec. 1 footnote), PCG 1e-4 relative with a
+ * 100-iteration stagnation window (App. B), A' threshold 1e-2 dhat, sigma
+ * growth 1.2 capped at 100 sigma0 (Alg. 1, Sec. 3.4), alpha_min 1e-9 (App. B). */
+typedef struct {
+  int32_t precision;          /* bal_precision */
+  int32_t precond;            /* bal_precond */
+  double pcg_tol;             /* ||r_k|| <= pcg_tol ||r_0|| */
+  int32_t pcg_max_iter;
+  int32_t pcg_stall_window;   /* stop if no new minimum residual in this many iterations */
+  double newton_tol;          /* ||e^l||_2 <= newton_tol ||e^0||_2 */
+  double newton_abs_tol;      /* or ||e^l||_2 <= newton_abs_tol */
+  int32_t newton_max_iter;
+  double ap_ratio;            /* A' threshold factor (1e-2) */
+  double sigma_growth;        /* 1.2 */
+  double sigma_cap;           /* 100 (times sigma0) */
+  int32_t sigma_literal_max;  /* 1 = printed max(1.2 s, 100 s0) rule */
+  double step_bound;          /* 0.9: alpha_0 <= step_bound d_i / Delta_i */
+  double ls_min_alpha;        /* 1e-9 (App. B) */
+  double ls_slack;            /* relative energy slack for rounding noise (1e-12) */
+  int64_t contact_cap;        /* Sec. 5.2 memory limit on |A| (line-search halving) */
+  int32_t ls_extra_pcg;       /* App. B: extra PCG iterations when alpha < ls_min_alpha */
+  double warm_tol;            /* warm-start subdomain PCG relative tolerance (1e-2) */
+  int32_t warm_max_iter;      /* warm-start subdomain PCG iteration cap (50) */
+  int32_t mixed_inner_max;    /* FP32 inner PCG iterations per refinement pass */
+  double mixed_inner_tol;     /* FP32 inner relative tolerance per pass */
+  int32_t mixed_max_refine;   /* max FP64 refinement passes */
+} bal_params;
+
+/* Scene description: HOST arrays, copied by bal_create_scene. */
+typedef struct {
+  int32_t n_verts, n_tets, n_tris, n_edges, n_surf_verts;
+  const double* X;            /* [n_verts][3] rest positions (m) */
+  const int32_t* tets;        /* [n_tets][4] positively oriented */
+  const int32_t* tris;        /* [n_tris][3] boundary triangles */
+  const int32_t* edges;       /* [n_edges][2] boundary edges, i < j, sorted unique */
+  const int32_t* surf_verts;  /* [n_surf_verts] boundary vertices */
+  const double* E;            /* [n_tets] Young's modulus (Pa) */
+  const double* nu;           /* [n_tets] Poisson ratio */
+  const double* rho;          /* [n_tets] density (kg/m^3) */
+  const uint8_t* pinned;      /* [n_verts] 1 = Dirichlet vertex */
+  double h;                   /* time step (s) */
+  double dhat;                /* contact offset (m) */
+  double gravity[3];          /* m/s^2 */
+  int64_t pair_capacity;      /* initial candidate-pair buffer (grows up to pair_limit) */
+  int64_t pair_limit;         /* hard limit; exceeding it returns BAL_ERR_CAPACITY */
+} bal_scene_desc;
+
+typedef struct bal_scene bal_scene;
+
+/* Read-only view of the assembled Hessian in symmetric lower storage
+ * H = D + L + L^T + C + C^T (Sec. 5.1, App. C): D = 3x3 diagonal blocks
+ * [n_verts][9]; L = static lower blocks in CSR (row_ptr[n_verts+1], col[nnz_L],
+ * val[nnz_L][9]); C = merged contact lower blocks (row[nnz_C], col[nnz_C],
+ * val[nnz_C][9]) sorted by (row, col). Blocks are row-major 3x3; a lower block
+ * at (row i, col j), i > j, holds H[3i..3i+2, 3j..3j+2]. Device pointers owned
+ * by the scene, valid until the next assemble call. */
+typedef struct {
+  int32_t n_verts;
+  int64_t nnz_L, nnz_C;
+  const double* D;
+  const int32_t* L_row_ptr;
+  const int32_t* L_col;
+  const double* L_val;
+  const int32_t* C_row;
+  const int32_t* C_col;
+  const double* C_val;
+  const double* Lambda;       /* [n_verts][3] assembled eigenvalue stiffness (Sec. 4.2.2) */
+} bal_bsr_view;
+
+/* Augmented-Lagrangian state of the current time step (Alg. 1). Arrays are
+ * HOST arrays. A pair key packs (kind << 62) | (first << 31) | second with
+ * kind 0 = point-triangle (vertex id, triangle index) and kind 1 = edge-edge
+ * (edge index, edge index, first < second). */
+typedef struct {
+  double sigma, sigma0;
+  double dmin_prev;
+  int64_t n_ap;               /* |A'| */
+  uint64_t* ap_keys;          /* [n_ap] sorted ascending */
+  double* ap_mu;              /* [n_ap] */
+} bal_al_state;
+
+typedef struct {
+  int32_t iters;              /* PCG iterations performed */
+  double rel_residual;        /* ||b - H x|| / ||b||, recomputed in FP64 */
+  double rel_residual_r0;     /* ||b - H x|| / ||r_0|| */
+  int32_t stagnated;          /* 1 if stopped by the stagnation window */
+  int32_t converged;          /* 1 if the tolerance was met */
+  int32_t refine_passes;      /* mixed precision: FP64 refinement passes */
+  int32_t warm_iters;         /* warm start: subdomain PCG iterations */
+  int32_t n_groups;           /* warm start: stiffness groups */
+} bal_solve_info;
+
+typedef struct {
+  int32_t l;                  /* iteration index inside the time step */
+  int32_t converged;          /* 1 if the convergence test passed (no step taken) */
+  int64_t n_active;           /* |A| at the iterate */
+  int64_t n_ap;               /* |A'| */
+  int64_t n_candidates;       /* line-search candidate pairs */
+  double dmin;                /* min distance over A (inf if empty) */
+  double sigma;
+  double grad_norm;           /* ||e^l||_2 */
+  double alpha;               /* accepted step length (0 if none) */
+  int32_t ls_trials;
+  int32_t pcg_iters;
+  double pcg_rel_residual;
+  double energy;              /* L_sigma at the accepted iterate */
+  double ms_assemble, ms_solve, ms_line_search, ms_contact;
+} bal_newton_info;
+
+typedef struct {
+  int32_t newton_iters;
+  int32_t pcg_iters_total;
+  int32_t converged;
+  int64_t max_active;
+  double min_distance;        /* min d over A seen at the iterates */
+  double sigma0, sigma_final;
+  double ms_total, ms_assemble, ms_solve, ms_line_search, ms_contact;
+} bal_step_info;
+
+/* ---- lifetime ------------------------------------------------------------ */
+const char* bal_last_error(void);
+void bal_default_params(bal_params* out);
+
+/* Copies the topology, precomputes D_m^{-1}, rest volumes, Lame parameters and
+ * lumped masses (Sec. 3.1), and builds the static lower BSR pattern with its
+ * element-to-slot map (Sec. 5.1, App. C). Allocates the scene's device
+ * buffers on the current device. */
+bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params,
+                            bal_scene** out);
+bal_status bal_destroy_scene(bal_scene* scene);
+bal_status bal_set_params(bal_scene* scene, const bal_params* params);
+bal_status bal_get_params(const bal_scene* scene, bal_params* out);
+/* Host copies of the static pattern: row_ptr [n_verts+1], col [nnz_L]; either
+ * may be NULL to query nnz only. */
+bal_status bal_static_pattern(const bal_scene* scene, int64_t* nnz_L, int32_t* row_ptr,
+                              int32_t* col);
+/* Lumped masses [n_verts] (host out). */
+bal_status bal_get_mass(const bal_scene* scene, double* mass_host);
+
+/* ---- time step state ------------------------------------------------------ */
+/* Starts a time step from (x_t, v_t) (device): y = x_t + h v_t + h^2 g
+ * (Sec. 3.1), A at x_t, sigma0 (Sec. 3.4), mu = 0, A' empty. */
+bal_status bal_step_begin(bal_scene* scene, const double* x_t, const double* v_t,
+                          void* stream);
+/* AL state of the current step. ap_keys / ap_mu may be NULL to query n_ap;
+ * otherwise they must hold `capacity` entries. */
+bal_status bal_get_al_state(const bal_scene* scene, bal_al_state* out, int64_t capacity);
+/* Replaces sigma, sigma0, dmin_prev and A' (host keys sorted ascending). */
+bal_status bal_set_al_state(bal_scene* scene, const bal_al_state* in);
+/* Inertia target y of the current step into y_out (device). */
+bal_status bal_get_y(const bal_scene* scene, double* y_out, void* stream);
+
+/* ---- hot-path calls --------------------------------------------------------- */
+/* Assembles at x (device) the gradient e = grad L_sigma (Eq. aug-lag; pinned
+ * entries zero) into grad_out (device, may be NULL) and the PSD-projected
+ * Hessian (elements: projection of dP/dF; contact stencils: projection of the
+ * 12x12 stencil Hessian; Sec. 4.2.2) into scene storage, with A = {d < dhat}
+ * found at x and A', mu, sigma from the current step state; s_i evaluated at x
+ * (Sec. 3.2.2). Pinned rows and columns are eliminated with diagonal m/h^2
+ * (App. C). Fills *view if non-NULL. */
+bal_status bal_assemble_hessian(bal_scene* scene, const double* x, double* grad_out,
+                                bal_bsr_view* view, void* stream);
+/* y = H v with the last assembled H (Sec. 5.1 SpMV; device in/out). */
+bal_status bal_spmv(bal_scene* scene, const double* v, double* y, void* stream);
+/* Solves H sol = rhs with block-Jacobi PCG (Sec. 4.2, App. B), optionally
+ * warm-started by the stiffness-grouped subdomain solve (Sec. 4.2.2), or in
+ * FP32 with FP64 iterative refinement, from sol_inout. Stops at
+ * ||r_k|| <= rel_tol ||r_0||, when the residual reaches no new minimum in
+ * pcg_stall_window iterations, or at max_iter. */
+bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* sol_inout,
+                         double rel_tol, int32_t max_iter, bal_solve_info* info,
+                         void* stream);
+/* L_sigma at x with A(x) and the step's A' state (host out). */
+bal_status bal_energy(bal_scene* scene, const double* x, double* energy_out, void* stream);
+/* One Alg. 1 iteration l on x_inout (device): dual update of the previous
+ * iteration, A, A' rule, gradient and convergence test, assembly, PCG, step
+ * bound, backtracking line search (Sec. 5.2 memory cap). */
+bal_status bal_newton_step(bal_scene* scene, double* x_inout, bal_newton_info* info,
+                           void* stream);
+/* Full time step: bal_step_begin + Alg. 1 loop + v = (x - x_t)/h (Sec. 3.1). */
+bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_inout,
+                         bal_step_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAL_H_ */
