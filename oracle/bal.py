@@ -21,7 +21,10 @@ paper used here (each one is recorded in the design notes):
   printed denominator is not squared, which is not dimensionally
   consistent), floored at mbar / (h^2 b''(dhat/2, dhat));
 * line search: alpha_0 = min(1, min over pairs of 0.9 d_i / Delta_i) where
-  Delta_i bounds how fast the pair can close along p; halve until no tet is
+  Delta_i = max |p_a - p_b| over a node of each primitive bounds how fast the
+  pair can close along p (a rigid translation closes nothing); the candidate
+  radius dhat + 2 max|p_v| / 0.9 contains every pair that can constrain alpha or
+  enter A during the step; halve until no tet is
   inverted, the number of active pairs is within the memory cap (Sec. 5.2),
   and L_sigma does not increase by more than a rounding slack.
 """
@@ -92,13 +95,18 @@ def make_pairset(model, x, A_keys, Ap, sigma):
     return PairSet(keys, inA, inAp, mu, s)
 
 
-def displacement_bound(pairs, p_norm, scene):
-    """Delta_i = max node speed on the first primitive + on the second."""
+def displacement_bound(pairs, p, scene):
+    """Delta_i = max over node a of the first primitive and node b of the second
+    of |p_a - p_b|. Every point of the two convex hulls moves by a convex
+    combination of node displacements, so the distance between the hulls can
+    shrink by at most alpha * Delta_i along x + alpha p."""
     nodes = contact.stencil_nodes(pairs, scene)
-    pn = p_norm[nodes]
+    P = p[nodes]                                      # [n,4,3]
     is_pt = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)[:, 0] == 0
-    return np.where(is_pt, pn[:, 0] + pn[:, 1:].max(axis=1),
-                    pn[:, :2].max(axis=1) + pn[:, 2:].max(axis=1))
+    nrm = lambda a, b: np.sqrt(np.sum((P[:, a] - P[:, b]) ** 2, axis=1))  # noqa: E731
+    pt = np.maximum(np.maximum(nrm(0, 1), nrm(0, 2)), nrm(0, 3))
+    ee = np.maximum(np.maximum(nrm(0, 2), nrm(0, 3)), np.maximum(nrm(1, 2), nrm(1, 3)))
+    return np.where(is_pt, pt, ee)
 
 
 def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
@@ -110,7 +118,7 @@ def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
     alpha = 1.0
     if cand:
         d0, _, _ = contact.pair_distances(x, cand, sc)
-        Dl = displacement_bound(cand, pnorm, sc)
+        Dl = displacement_bound(cand, p, sc)
         m = prm.step_bound * d0 < Dl
         if np.any(m):
             alpha = min(1.0, float(np.min(prm.step_bound * d0[m] / Dl[m])))

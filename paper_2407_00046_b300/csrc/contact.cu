@@ -1,0 +1,630 @@
+// Contact stencils on the GPU, FP64: unsigned point-triangle / edge-edge
+// distances with region classification, the IPC clamped log barrier and the
+// augmented-Lagrangian terms of Eq. (aug-lag), PSD projection of the 12x12
+// stencil Hessian (Sec. 4.2.2), energies for the line search, the conservative
+// step bound and the dual update of Algorithm 1.
+//
+// Region decisions (which closest-feature formula applies) and the distances
+// used for set membership are computed with explicitly rounded operations
+// (no fused multiply-add), so they round exactly like a plain left-to-right
+// FP64 evaluation of the same formulas.
+#include <cub/cub.cuh>
+
+#include "scene.cuh"
+
+namespace bal {
+
+namespace {
+
+enum { R_PP = 0, R_PE = 1, R_PT = 2, R_EE = 3 };
+struct Region {
+  int kind;
+  int n[4];   // PP: (i, j); PE: (p, a, b); PT/EE: (0, 1, 2, 3)
+};
+
+// ---- explicitly rounded helpers ------------------------------------------------
+__device__ inline d3 sub_rn(d3 a, d3 b) {
+  return d3{__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)};
+}
+__device__ inline double dot_rn(d3 a, d3 b) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+__device__ inline d3 cross_rn(d3 a, d3 b) {
+  return d3{__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)),
+            __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+            __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+}
+
+// closest point on segment ab to p: squared distance, kind, which end (PP)
+__device__ inline void seg_candidate(d3 p, d3 a, d3 b, double& d2, int& kind, int& end) {
+  const d3 ab = sub_rn(b, a);
+  const double L2 = dot_rn(ab, ab);
+  const double u = L2 > 0.0 ? __ddiv_rn(dot_rn(sub_rn(p, a), ab), L2) : 0.0;
+  if (u <= 0.0) {
+    const d3 r = sub_rn(p, a);
+    d2 = dot_rn(r, r);
+    kind = R_PP;
+    end = 0;
+  } else if (u >= 1.0) {
+    const d3 r = sub_rn(p, b);
+    d2 = dot_rn(r, r);
+    kind = R_PP;
+    end = 1;
+  } else {
+    const d3 c = d3{__dadd_rn(a.x, __dmul_rn(u, ab.x)), __dadd_rn(a.y, __dmul_rn(u, ab.y)),
+                    __dadd_rn(a.z, __dmul_rn(u, ab.z))};
+    const d3 r = sub_rn(p, c);
+    d2 = dot_rn(r, r);
+    kind = R_PE;
+    end = 0;
+  }
+}
+
+__device__ inline Region make_seg_region(int kind, int end, int ip, int ia, int ib) {
+  Region R;
+  R.kind = kind;
+  if (kind == R_PE) {
+    R.n[0] = ip; R.n[1] = ia; R.n[2] = ib; R.n[3] = -1;
+  } else {
+    R.n[0] = ip; R.n[1] = end ? ib : ia; R.n[2] = -1; R.n[3] = -1;
+  }
+  return R;
+}
+
+__device__ Region classify_pt(const d3 X[4]) {
+  const d3 e1 = sub_rn(X[2], X[1]), e2 = sub_rn(X[3], X[1]), r = sub_rn(X[0], X[1]);
+  const double a11 = dot_rn(e1, e1), a12 = dot_rn(e1, e2), a22 = dot_rn(e2, e2);
+  const double b1 = dot_rn(e1, r), b2 = dot_rn(e2, r);
+  const double det = __dsub_rn(__dmul_rn(a11, a22), __dmul_rn(a12, a12));
+  if (det > 0.0) {
+    const double be1 = __ddiv_rn(__dsub_rn(__dmul_rn(a22, b1), __dmul_rn(a12, b2)), det);
+    const double be2 = __ddiv_rn(__dsub_rn(__dmul_rn(a11, b2), __dmul_rn(a12, b1)), det);
+    const double be0 = __dsub_rn(__dsub_rn(1.0, be1), be2);
+    if (be0 > 0.0 && be1 > 0.0 && be2 > 0.0) {
+      Region R;
+      R.kind = R_PT;
+      R.n[0] = 0; R.n[1] = 1; R.n[2] = 2; R.n[3] = 3;
+      return R;
+    }
+  }
+  const int ea[3] = {1, 2, 3}, eb[3] = {2, 3, 1};
+  double best = 0.0;
+  int bk = 0, bkind = 0, bend = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double d2;
+    int kind, end;
+    seg_candidate(X[0], X[ea[k]], X[eb[k]], d2, kind, end);
+    if (k == 0 || d2 < best) {
+      best = d2; bk = k; bkind = kind; bend = end;
+    }
+  }
+  return make_seg_region(bkind, bend, 0, ea[bk], eb[bk]);
+}
+
+__device__ Region classify_ee(const d3 X[4]) {
+  const d3 u = sub_rn(X[1], X[0]), v = sub_rn(X[3], X[2]), w = sub_rn(X[0], X[2]);
+  const double A = dot_rn(u, u), B = dot_rn(u, v), C = dot_rn(v, v), D = dot_rn(u, w),
+               Ev = dot_rn(v, w);
+  const d3 n = cross_rn(u, v);
+  const double den = dot_rn(n, n);
+  if (den > __dmul_rn(__dmul_rn(1e-12, A), C)) {
+    const double s = __ddiv_rn(__dsub_rn(__dmul_rn(B, Ev), __dmul_rn(C, D)), den);
+    const double t = __ddiv_rn(__dsub_rn(__dmul_rn(A, Ev), __dmul_rn(B, D)), den);
+    if (s > 0.0 && s < 1.0 && t > 0.0 && t < 1.0) {
+      Region R;
+      R.kind = R_EE;
+      R.n[0] = 0; R.n[1] = 1; R.n[2] = 2; R.n[3] = 3;
+      return R;
+    }
+  }
+  const int ip[4] = {0, 1, 2, 3}, ia[4] = {2, 2, 0, 0}, ib[4] = {3, 3, 1, 1};
+  double best = 0.0;
+  int bk = 0, bkind = 0, bend = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double d2;
+    int kind, end;
+    seg_candidate(X[ip[k]], X[ia[k]], X[ib[k]], d2, kind, end);
+    if (k == 0 || d2 < best) {
+      best = d2; bk = k; bkind = kind; bend = end;
+    }
+  }
+  return make_seg_region(bkind, bend, ip[bk], ia[bk], ib[bk]);
+}
+
+// distance of the region formula, explicitly rounded
+__device__ double region_distance(const d3 X[4], const Region& R) {
+  if (R.kind == R_PP) {
+    const d3 r = sub_rn(X[R.n[0]], X[R.n[1]]);
+    return __dsqrt_rn(dot_rn(r, r));
+  }
+  if (R.kind == R_PE) {
+    const d3 e = sub_rn(X[R.n[2]], X[R.n[1]]);
+    const d3 c = cross_rn(sub_rn(X[R.n[0]], X[R.n[1]]), e);
+    return __dsqrt_rn(__ddiv_rn(dot_rn(c, c), dot_rn(e, e)));
+  }
+  if (R.kind == R_PT) {
+    const d3 nrm = cross_rn(sub_rn(X[2], X[1]), sub_rn(X[3], X[1]));
+    return __ddiv_rn(fabs(dot_rn(sub_rn(X[0], X[1]), nrm)), __dsqrt_rn(dot_rn(nrm, nrm)));
+  }
+  const d3 nrm = cross_rn(sub_rn(X[1], X[0]), sub_rn(X[3], X[2]));
+  return __ddiv_rn(fabs(dot_rn(sub_rn(X[0], X[2]), nrm)), __dsqrt_rn(dot_rn(nrm, nrm)));
+}
+
+__device__ inline void pair_nodes(const Dev& S, uint64_t key, int v[4]) {
+  const uint32_t a = key_a(key), b = key_b(key);
+  if (key_kind(key) == 0) {
+    v[0] = (int)a;
+    v[1] = S.tris[3 * (int64_t)b];
+    v[2] = S.tris[3 * (int64_t)b + 1];
+    v[3] = S.tris[3 * (int64_t)b + 2];
+  } else {
+    v[0] = S.edges[2 * (int64_t)a];
+    v[1] = S.edges[2 * (int64_t)a + 1];
+    v[2] = S.edges[2 * (int64_t)b];
+    v[3] = S.edges[2 * (int64_t)b + 1];
+  }
+}
+
+__device__ inline double pair_distance(const Dev& S, const double* __restrict__ x, uint64_t key,
+                                       int v[4], d3 X[4], Region& R) {
+  pair_nodes(S, key, v);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) X[a] = ld3(x, v[a]);
+  R = key_kind(key) == 0 ? classify_pt(X) : classify_ee(X);
+  return region_distance(X, R);
+}
+
+// ---- barrier (Sec. 3.3) ------------------------------------------------------------
+__device__ inline double bar(double d, double c) {
+  if (!(d > 0.0)) return INFINITY;
+  if (d >= c) return 0.0;
+  const double t = d - c;
+  return -t * t * log(d / c);
+}
+__device__ inline double dbar(double d, double c) {
+  if (!(d > 0.0) || d >= c) return 0.0;
+  const double t = d - c;
+  return -2.0 * t * log(d / c) - t * t / d;
+}
+__device__ inline double d2bar(double d, double c) {
+  if (!(d > 0.0) || d >= c) return 0.0;
+  const double t = d - c;
+  return -2.0 * log(d / c) - 4.0 * t / d + t * t / (d * d);
+}
+
+// ---- derivatives of d^2 (hand-derived, per region) ----------------------------------
+// Variables are differences of stencil nodes: var_k = sum_n C[k][n] X[n] with C in
+// {-1,0,1}. f = d^2(vars); fk[k] = df/dvar_k; Fkl[k][l] = d2f/dvar_k dvar_l (3x3).
+struct VarSpace {
+  int nvar;
+  int C[3][4];
+  d3 fk[3];
+  double Fkl[3][3][3][3];
+  double f;
+};
+
+__device__ inline void outer_acc(double M[3][3], double s, d3 a, d3 b) {
+  const double av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] += s * av[i] * bv[j];
+}
+__device__ inline void skew_acc(double M[3][3], double s, d3 a) {   // M += s [a]x
+  M[0][1] -= s * a.z; M[0][2] += s * a.y;
+  M[1][0] += s * a.z; M[1][2] -= s * a.x;
+  M[2][0] -= s * a.y; M[2][1] += s * a.x;
+}
+__device__ inline void eye_acc(double M[3][3], double s) {
+  M[0][0] += s; M[1][1] += s; M[2][2] += s;
+}
+
+__device__ void d2_derivs(const d3 X[4], const Region& R, VarSpace& V) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int n = 0; n < 4; ++n) V.C[k][n] = 0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V.Fkl[k][l][i][j] = 0.0;
+  }
+  if (R.kind == R_PP) {
+    V.nvar = 1;
+    V.C[0][R.n[0]] = 1;
+    V.C[0][R.n[1]] = -1;
+    const d3 r = X[R.n[0]] - X[R.n[1]];
+    V.f = dot(r, r);
+    V.fk[0] = 2.0 * r;
+    eye_acc(V.Fkl[0][0], 2.0);
+    return;
+  }
+  if (R.kind == R_PE) {
+    V.nvar = 2;
+    V.C[0][R.n[0]] = 1; V.C[0][R.n[1]] = -1;   // u = p - a
+    V.C[1][R.n[2]] = 1; V.C[1][R.n[1]] = -1;   // e = b - a
+    const d3 u = X[R.n[0]] - X[R.n[1]], e = X[R.n[2]] - X[R.n[1]];
+    const double k = dot(u, e), L = dot(e, e), iL = 1.0 / L;
+    V.f = dot(u, u) - k * k * iL;
+    V.fk[0] = 2.0 * u - (2.0 * k * iL) * e;
+    V.fk[1] = (2.0 * k * k * iL * iL) * e - (2.0 * k * iL) * u;
+    eye_acc(V.Fkl[0][0], 2.0);
+    outer_acc(V.Fkl[0][0], -2.0 * iL, e, e);
+    outer_acc(V.Fkl[0][1], -2.0 * iL, e, u);
+    eye_acc(V.Fkl[0][1], -2.0 * k * iL);
+    outer_acc(V.Fkl[0][1], 4.0 * k * iL * iL, e, e);
+    outer_acc(V.Fkl[1][1], -2.0 * iL, u, u);
+    outer_acc(V.Fkl[1][1], 4.0 * k * iL * iL, u, e);
+    outer_acc(V.Fkl[1][1], 4.0 * k * iL * iL, e, u);
+    eye_acc(V.Fkl[1][1], 2.0 * k * k * iL * iL);
+    outer_acc(V.Fkl[1][1], -8.0 * k * k * iL * iL * iL, e, e);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) V.Fkl[1][0][i][j] = V.Fkl[0][1][j][i];
+    return;
+  }
+  // plane distance: f = u^2 / w, u = r . (a x b), w = |a x b|^2
+  V.nvar = 3;
+  d3 r, a, b;
+  if (R.kind == R_PT) {   // r = X0 - X1, a = X2 - X1, b = X3 - X1
+    V.C[0][0] = 1; V.C[0][1] = -1;
+    V.C[1][2] = 1; V.C[1][1] = -1;
+    V.C[2][3] = 1; V.C[2][1] = -1;
+    r = X[0] - X[1]; a = X[2] - X[1]; b = X[3] - X[1];
+  } else {                // r = X0 - X2, a = X1 - X0, b = X3 - X2
+    V.C[0][0] = 1; V.C[0][2] = -1;
+    V.C[1][1] = 1; V.C[1][0] = -1;
+    V.C[2][3] = 1; V.C[2][2] = -1;
+    r = X[0] - X[2]; a = X[1] - X[0]; b = X[3] - X[2];
+  }
+  const d3 n = cross(a, b);
+  const double u = dot(r, n), w = dot(n, n), iw = 1.0 / w;
+  const d3 gu[3] = {n, cross(b, r), cross(r, a)};
+  const d3 gw[3] = {d3{0, 0, 0}, 2.0 * cross(b, n), 2.0 * cross(n, a)};
+  V.f = u * u * iw;
+  const double c_u = 2.0 * u * iw, c_w = -u * u * iw * iw;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) V.fk[k] = c_u * gu[k] + c_w * gw[k];
+  const double al = 2.0 * iw, be = -2.0 * u * iw * iw, ga = 2.0 * u * u * iw * iw * iw;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      outer_acc(V.Fkl[k][l], al, gu[k], gu[l]);
+      outer_acc(V.Fkl[k][l], be, gu[k], gw[l]);
+      outer_acc(V.Fkl[k][l], be, gw[k], gu[l]);
+      outer_acc(V.Fkl[k][l], ga, gw[k], gw[l]);
+    }
+  // + (2u/w) Hess u : U_ra = -[b]x, U_rb = [a]x, U_ab = -[r]x (and transposes)
+  const double su = 2.0 * u * iw;
+  skew_acc(V.Fkl[0][1], -su, b);
+  skew_acc(V.Fkl[1][0], su, b);
+  skew_acc(V.Fkl[0][2], su, a);
+  skew_acc(V.Fkl[2][0], -su, a);
+  skew_acc(V.Fkl[1][2], -su, r);
+  skew_acc(V.Fkl[2][1], su, r);
+  // - (u^2/w^2) Hess w : W_aa = 2(|b|^2 I - b b^T), W_bb = 2(|a|^2 I - a a^T),
+  //                      W_ab = 2(2 a b^T - (a.b) I - b a^T)
+  const double sw = -u * u * iw * iw;
+  eye_acc(V.Fkl[1][1], 2.0 * sw * dot(b, b));
+  outer_acc(V.Fkl[1][1], -2.0 * sw, b, b);
+  eye_acc(V.Fkl[2][2], 2.0 * sw * dot(a, a));
+  outer_acc(V.Fkl[2][2], -2.0 * sw, a, a);
+  outer_acc(V.Fkl[1][2], 4.0 * sw, a, b);
+  eye_acc(V.Fkl[1][2], -2.0 * sw * dot(a, b));
+  outer_acc(V.Fkl[1][2], -2.0 * sw, b, a);
+  outer_acc(V.Fkl[2][1], 4.0 * sw, b, a);
+  eye_acc(V.Fkl[2][1], -2.0 * sw * dot(a, b));
+  outer_acc(V.Fkl[2][1], -2.0 * sw, a, b);
+}
+
+// ---- 12x12 symmetric eigen-decomposition by cyclic Jacobi ------------------------
+// A (row-major 144) is overwritten (diagonal = eigenvalues); Q gets the eigenvectors
+// in its columns. Bounded sweep count; off-diagonal mass checked every sweep.
+__device__ void jacobi12(double* A, double* Q) {
+  for (int i = 0; i < 144; ++i) Q[i] = (i % 13 == 0) ? 1.0 : 0.0;
+  double fro = 0.0;
+  for (int i = 0; i < 144; ++i) fro += A[i] * A[i];
+  if (fro == 0.0) return;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < 12; ++p)
+      for (int q = p + 1; q < 12; ++q) off += A[12 * p + q] * A[12 * p + q];
+    if (off <= 1e-32 * fro) break;
+    for (int p = 0; p < 11; ++p) {
+      for (int q = p + 1; q < 12; ++q) {
+        const double apq = A[12 * p + q];
+        if (fabs(apq) <= 1e-300) continue;
+        const double app = A[13 * p], aqq = A[13 * q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < 12; ++r) {
+          if (r == p || r == q) continue;
+          const double arp = A[12 * r + p], arq = A[12 * r + q];
+          const double nrp = c * arp - s * arq, nrq = s * arp + c * arq;
+          A[12 * r + p] = A[12 * p + r] = nrp;
+          A[12 * r + q] = A[12 * q + r] = nrq;
+        }
+        A[13 * p] = app - t * apq;
+        A[13 * q] = aqq + t * apq;
+        A[12 * p + q] = A[12 * q + p] = 0.0;
+        for (int r = 0; r < 12; ++r) {
+          const double vrp = Q[12 * r + p], vrq = Q[12 * r + q];
+          Q[12 * r + p] = c * vrp - s * vrq;
+          Q[12 * r + q] = s * vrp + c * vrq;
+        }
+      }
+    }
+  }
+}
+
+struct ContactArgs {
+  const uint64_t* keys;
+  const uint8_t* flags;
+  const double* mu;
+  const double* s;
+  int64_t n;
+  double sigma;
+  double* grad;
+  int hess;
+  uint64_t* emit_keys;   // [n][6]
+  double* emit_vals;     // [n][6][9]
+};
+
+__global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __restrict__ x,
+                                                       ContactArgs A) {
+  double H[144], Q[144];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = A.keys[i];
+    int v[4];
+    d3 X[4];
+    Region R;
+    pair_distance(S, x, key, v, X, R);
+    VarSpace V;
+    d2_derivs(X, R, V);
+    const double d = sqrt(V.f);
+    const uint8_t fl = A.flags[i];
+    const double inA = (fl & PF_A) ? 1.0 : 0.0, inAp = (fl & PF_AP) ? 1.0 : 0.0;
+    const double c2 = S.dhat + A.s[i];
+    const double p1 = inA * A.sigma * dbar(d, S.dhat) + inAp * (-A.mu[i] + A.sigma * dbar(d, c2));
+    const double p2 = inA * A.sigma * d2bar(d, S.dhat) + inAp * A.sigma * d2bar(d, c2);
+    // g2 = grad(d^2) on the 12 stencil DOFs
+    double g2[12];
+#pragma unroll
+    for (int nd = 0; nd < 4; ++nd) {
+      d3 acc = d3{0, 0, 0};
+      for (int k = 0; k < V.nvar; ++k)
+        if (V.C[k][nd] != 0) acc = acc + (double)V.C[k][nd] * V.fk[k];
+      g2[3 * nd] = acc.x; g2[3 * nd + 1] = acc.y; g2[3 * nd + 2] = acc.z;
+    }
+    const double cg = p1 / (2.0 * d);
+    bool pin[4];
+#pragma unroll
+    for (int nd = 0; nd < 4; ++nd) {
+      pin[nd] = S.pinned[v[nd]] != 0;
+      if (!pin[nd] && A.grad)
+        atomic_add3(A.grad, v[nd], d3{cg * g2[3 * nd], cg * g2[3 * nd + 1], cg * g2[3 * nd + 2]});
+    }
+    if (!A.hess) continue;
+    // H = c1 g2 g2^T + c2 Hess(d^2)
+    const double c1 = (p2 - p1 / d) / (4.0 * d * d), cc2 = p1 / (2.0 * d);
+    for (int nd = 0; nd < 4; ++nd)
+      for (int md = 0; md < 4; ++md)
+        for (int ii = 0; ii < 3; ++ii)
+          for (int jj = 0; jj < 3; ++jj) {
+            double h2 = 0.0;
+            for (int k = 0; k < V.nvar; ++k) {
+              const int ck = V.C[k][nd];
+              if (!ck) continue;
+              for (int l = 0; l < V.nvar; ++l) {
+                const int cl = V.C[l][md];
+                if (cl) h2 += (double)(ck * cl) * V.Fkl[k][l][ii][jj];
+              }
+            }
+            const int r = 3 * nd + ii, c = 3 * md + jj;
+            H[12 * r + c] = c1 * g2[r] * g2[c] + cc2 * h2;
+          }
+    // symmetrise, project to PSD
+    for (int r = 0; r < 12; ++r)
+      for (int c = r + 1; c < 12; ++c) {
+        const double m = 0.5 * (H[12 * r + c] + H[12 * c + r]);
+        H[12 * r + c] = H[12 * c + r] = m;
+      }
+    jacobi12(H, Q);
+    double lam[12], tr = 0.0;
+    for (int k = 0; k < 12; ++k) {
+      lam[k] = H[13 * k] > 0.0 ? H[13 * k] : 0.0;
+      tr += lam[k];
+    }
+    tr *= (1.0 / 12.0);
+    for (int r = 0; r < 12; ++r)
+      for (int c = r; c < 12; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < 12; ++k) acc += Q[12 * r + k] * lam[k] * Q[12 * c + k];
+        H[12 * r + c] = H[12 * c + r] = acc;
+      }
+#pragma unroll
+    for (int nd = 0; nd < 4; ++nd) {
+      atomicAdd(S.Lambda + 3 * v[nd], tr);
+      atomicAdd(S.Lambda + 3 * v[nd] + 1, tr);
+      atomicAdd(S.Lambda + 3 * v[nd] + 2, tr);
+      if (!pin[nd]) {
+        double* Dd = S.D + 9 * (int64_t)v[nd];
+        for (int ii = 0; ii < 3; ++ii)
+          for (int jj = 0; jj < 3; ++jj) atomicAdd(Dd + 3 * ii + jj, H[12 * (3 * nd + ii) + 3 * nd + jj]);
+      }
+    }
+    // off-diagonal lower blocks -> (key = row << 32 | col, value) for the segmented reduction
+    const int pa[6] = {1, 2, 3, 2, 3, 3};
+    const int pb[6] = {0, 0, 0, 1, 1, 2};
+    for (int k = 0; k < 6; ++k) {
+      const int a = pa[k], b = pb[k];
+      uint64_t* ek = A.emit_keys + 6 * i + k;
+      double* ev = A.emit_vals + 9 * (6 * i + k);
+      if (pin[a] || pin[b]) {
+        *ek = ~0ull;
+        continue;
+      }
+      const bool a_row = v[a] > v[b];
+      const int rn = a_row ? a : b, cn = a_row ? b : a;
+      *ek = ((uint64_t)(uint32_t)v[rn] << 32) | (uint32_t)v[cn];
+      for (int ii = 0; ii < 3; ++ii)
+        for (int jj = 0; jj < 3; ++jj) ev[3 * ii + jj] = H[12 * (3 * rn + ii) + 3 * cn + jj];
+    }
+  }
+}
+
+__global__ void k_pair_distance(Dev S, const double* __restrict__ x, const uint64_t* __restrict__ keys,
+                                int64_t n, double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    d[i] = pair_distance(S, x, keys[i], v, X, R);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __restrict__ x,
+                                                       const uint64_t* __restrict__ cand, int64_t nc,
+                                                       const uint64_t* __restrict__ apk,
+                                                       const double* __restrict__ apmu,
+                                                       const double* __restrict__ aps, int64_t nap,
+                                                       double sigma, double* partials, int nblk) {
+  double e = 0.0, cnt = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const double d = pair_distance(S, x, cand[i], v, X, R);
+    if (d < S.dhat) {
+      e += sigma * bar(d, S.dhat);
+      cnt += 1.0;
+    }
+  }
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nap; i += (int64_t)gridDim.x * NT) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const double d = pair_distance(S, x, apk[i], v, X, R);
+    const double c2 = S.dhat + aps[i];
+    e += apmu[i] * (c2 - d) + sigma * bar(d, c2);
+  }
+  e = block_sum<double, NT>(e);
+  cnt = block_sum<double, NT>(cnt);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = e;
+    partials[nblk + blockIdx.x] = cnt;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restrict__ x,
+                                                   const double* __restrict__ pn,
+                                                   const uint64_t* __restrict__ cand, int64_t nc,
+                                                   double eta, double* partials) {
+  double amin = 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const uint64_t key = cand[i];
+    const double d = pair_distance(S, x, key, v, X, R);
+    double Dl;
+    if (key_kind(key) == 0)
+      Dl = pn[v[0]] + fmax(pn[v[1]], fmax(pn[v[2]], pn[v[3]]));
+    else
+      Dl = fmax(pn[v[0]], pn[v[1]]) + fmax(pn[v[2]], pn[v[3]]);
+    if (eta * d < Dl) amin = fmin(amin, eta * d / Dl);
+  }
+  amin = block_min<double, NT>(amin, 1.0);
+  if (threadIdx.x == 0) partials[blockIdx.x] = amin;
+}
+
+__global__ void k_dual_update(Dev S, const double* __restrict__ x, const uint64_t* __restrict__ keys,
+                              double* __restrict__ mu, int64_t n, double sigma) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const double d = pair_distance(S, x, keys[i], v, X, R);
+    const double m = mu[i];
+    const double s = fmax(-m / sigma - S.dhat + d, 0.0);
+    mu[i] = m + sigma * bar(d, S.dhat + s);
+  }
+}
+
+}  // namespace
+
+bal_status launch_pair_distance(Scene& S, const double* x, const uint64_t* keys, int64_t n,
+                                double* d, cudaStream_t st) {
+  if (n <= 0) return BAL_OK;
+  k_pair_distance<<<grid_for(n), kThreads, 0, st>>>(S.d, x, keys, n, d);
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
+}
+
+bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool hess,
+                                cudaStream_t st) {
+  if (S.n_eval <= 0) return BAL_OK;
+  ContactArgs A;
+  A.keys = S.eval_keys.as<uint64_t>();
+  A.flags = S.eval_flags.as<uint8_t>();
+  A.mu = S.eval_mu.as<double>();
+  A.s = S.eval_s.as<double>();
+  A.n = S.n_eval;
+  A.sigma = S.sigma;
+  A.grad = grad;
+  A.hess = hess ? 1 : 0;
+  if (hess) {
+    BAL_TRY(buf_reserve(S.emit_keys, sizeof(uint64_t) * 6 * S.n_eval));
+    BAL_TRY(buf_reserve(S.emit_vals, sizeof(double) * 54 * S.n_eval));
+  }
+  A.emit_keys = S.emit_keys.as<uint64_t>();
+  A.emit_vals = S.emit_vals.as<double>();
+  k_contact_terms<<<grid_for(S.n_eval, 128, kNumSM * 8), 128, 0, st>>>(S.d, x, A);
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
+}
+
+bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand, int64_t ncand,
+                                 int slot, cudaStream_t st) {
+  constexpr int NT = 256;
+  const int nblk = 2 * kNumSM;
+  const int64_t nap = (int64_t)S.ap_keys.size();
+  k_contact_energy<NT><<<nblk, NT, 0, st>>>(S.d, x, cand, ncand, S.ap_keys_d.as<uint64_t>(),
+                                            S.ap_mu_d.as<double>(), S.ap_s_d.as<double>(), nap,
+                                            S.sigma, S.partials, nblk);
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(finish_reduce_offset(S, 0, nblk, slot, RED_SUM, st));
+  BAL_TRY(finish_reduce_offset(S, nblk, nblk, slot + 1, RED_SUM, st));
+  return BAL_OK;
+}
+
+bal_status launch_step_bound(Scene& S, const double* x, const double* pnorm,
+                             const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st) {
+  constexpr int NT = 256;
+  const int nblk = 2 * kNumSM;
+  k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, pnorm, cand, ncand, S.prm.step_bound, S.partials);
+  BAL_LAUNCH_CHECK();
+  return finish_reduce(S, nblk, slot, RED_MIN, st);
+}
+
+bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t st) {
+  if (n <= 0) return BAL_OK;
+  k_dual_update<<<grid_for(n), kThreads, 0, st>>>(S.d, x, S.ap_keys_d.as<uint64_t>(),
+                                                 S.ap_mu_d.as<double>(), n, S.sigma);
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
+}
+
+}  // namespace bal

@@ -1,0 +1,162 @@
+// Internal scene state of libbal and the host-side launchers of each kernel
+// family. Everything here is private to the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace bal {
+
+// Device buffer with a capacity (bytes); grown with cudaMalloc outside the hot loop.
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+bal_status buf_reserve(Buf& b, size_t bytes);
+void buf_free(Buf& b);
+
+// Pair keys: (kind << 62) | (first << 31) | second.
+__host__ __device__ inline uint64_t pair_key(int kind, uint32_t a, uint32_t b) {
+  return ((uint64_t)kind << 62) | ((uint64_t)a << 31) | (uint64_t)b;
+}
+__host__ __device__ inline int key_kind(uint64_t k) { return (int)(k >> 62); }
+__host__ __device__ inline uint32_t key_a(uint64_t k) { return (uint32_t)((k >> 31) & 0x7fffffffu); }
+__host__ __device__ inline uint32_t key_b(uint64_t k) { return (uint32_t)(k & 0x7fffffffu); }
+
+// Per-pair flags of the evaluation list (A union A').
+enum : uint8_t { PF_A = 1, PF_AP = 2 };
+
+// Device-resident PCG scalars (one solve at a time per scene).
+struct PcgScalars {
+  double rz, pq, alpha, beta;
+  double r0norm, rnorm, bnorm, best;
+  double tol_abs;
+  int32_t it, best_it, done, stagnated, converged, max_it, window, pad;
+  uint32_t counter;   // last-block counter of the fused reductions
+  uint32_t counter2;
+};
+
+// Plain-old-data view of the scene's fixed device arrays, passed by value to kernels.
+struct Dev {
+  int32_t nv = 0, nt = 0, nf = 0, ne = 0, nsv = 0;
+  int64_t nnzL = 0;
+  double h = 0, dhat = 0;
+  // topology + rest data
+  const int32_t *tets = nullptr, *tris = nullptr, *edges = nullptr, *surf = nullptr;
+  const uint8_t* pinned = nullptr;
+  const double *Dm_inv = nullptr, *vol = nullptr, *mu = nullptr, *lam = nullptr, *mass = nullptr;
+  // static lower pattern: CSR + per-block row, element -> slot map
+  const int32_t *L_row_ptr = nullptr, *L_col = nullptr, *L_row = nullptr;
+  const int32_t* tet_slot = nullptr;  // [nt][6]: 2*slot + (1 if the stored block is the transpose)
+  // assembled matrix
+  double *D = nullptr, *Dinv = nullptr, *Lval = nullptr, *Lambda = nullptr;
+  // step vectors
+  double* y = nullptr;
+};
+
+struct Scene {
+  Dev d;
+  int32_t& nv() { return d.nv; }
+  double grav[3] = {0, 0, 0};
+  double mean_edge = 0;   // mean rest surface edge length (grid cell sizing)
+  double mbar = 0;        // mean lumped mass
+  bal_params prm{};
+  int64_t pair_limit = 0;
+  std::vector<double> mass_h;
+  std::vector<int32_t> row_ptr_h, col_h;
+  std::vector<void*> owned;   // fixed device allocations freed at destroy
+
+  // contact part of the matrix
+  int64_t nnzC = 0;
+  Buf C_row, C_col, C_val;
+  bool assembled = false;
+
+  // contact emission + sort scratch
+  Buf emit_keys, emit_keys_alt, emit_idx, emit_idx_alt, emit_vals, seg_head, seg_pos;
+  Buf cub_tmp;
+
+  // broad phase scratch
+  Buf bp_cells, bp_cells_alt, bp_ids, bp_ids_alt, bp_count, bp_offs;
+  Buf cand, cand_alt;            // candidates at r = dhat (sorted keys)
+  int64_t n_cand = 0;
+  Buf dist;                      // per-pair distances scratch
+  Buf eval_keys, eval_flags, eval_mu, eval_s;   // evaluation list A u A'
+  int64_t n_eval = 0;
+  Buf ls_cand, ls_cand_alt;      // line-search candidates
+  int64_t n_ls_cand = 0;
+
+  // vectors (device, 3*nv doubles each)
+  double *xt = nullptr, *grad = nullptr, *gtmp = nullptr, *xtrial = nullptr, *dir = nullptr;
+  double *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_x = nullptr;
+  double* pnorm = nullptr;       // [nv] |p_v|
+  // reductions
+  double* partials = nullptr;    // [kMaxPartials]
+  double* scal = nullptr;        // [64] scalar results
+  PcgScalars* pcg = nullptr;
+
+  // AL state of the current time step (host copy is authoritative)
+  bool step_active = false;
+  double sigma = 0, sigma0 = 0, dmin_prev = 0, e0 = 0;
+  int32_t l = 0;
+  std::vector<uint64_t> ap_keys;
+  std::vector<double> ap_mu;
+  Buf ap_keys_d, ap_mu_d, ap_s_d;   // device copy of A' (keys, mu, s fixed in the iteration)
+};
+
+constexpr int kMaxPartials = 4096;
+
+// ---- elastic.cu ---------------------------------------------------------------
+// grad (+)= inertia + elastic gradient (pinned zeroed); init=true overwrites.
+bal_status launch_inertia_elastic_grad(Scene& S, const double* x, double* grad,
+                                       cudaStream_t st);
+// D = m/h^2 I, Lval = 0, Lambda = m/h^2; then element Hessian blocks (projected)
+// and their mean eigenvalue into Lambda.
+bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st);
+// partial sums of (inertia, elastic) energy and an inversion count; result in
+// S.scal[0] (inertia), S.scal[1] (elastic), S.scal[2] (number of tets with J <= 0).
+bal_status launch_elastic_energy(Scene& S, const double* x, cudaStream_t st);
+
+// ---- contact.cu ---------------------------------------------------------------
+// distances of n pairs (keys) at x into d (device).
+bal_status launch_pair_distance(Scene& S, const double* x, const uint64_t* keys, int64_t n,
+                                double* d, cudaStream_t st);
+// gradient (+=) and, if hess, projected Hessian blocks of the eval list.
+bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool hess,
+                                cudaStream_t st);
+// sum over eval-like arrays of phi (barrier for A members at d<dhat, AL for A').
+// Writes S.scal[slot] = contact energy, S.scal[slot+1] = count of d < dhat over keys.
+bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand, int64_t ncand,
+                                 int slot, cudaStream_t st);
+// min over candidates of step_bound*d/Delta (where step_bound*d < Delta) -> S.scal[slot].
+bal_status launch_step_bound(Scene& S, const double* x, const double* pnorm,
+                             const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st);
+// A' dual update: s_i, mu_i += sigma b(d_i, dhat + s_i) for the device A' list.
+bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t st);
+
+// ---- broadphase.cu -------------------------------------------------------------
+// All PT/EE pairs whose primitives' (AABB) distance can be below r, sorted, in
+// out (grown as needed). Returns the count in *n.
+bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt,
+                           int64_t* n, cudaStream_t st);
+
+// ---- matrix.cu -----------------------------------------------------------------
+bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
+bal_status launch_dinv(Scene& S, cudaStream_t st);
+bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
+bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
+                     bal_solve_info* info, cudaStream_t st);
+
+// ---- reductions helper (matrix.cu) -----------------------------------------------
+// S.scal[slot] = sum / min / max of partials[0..n)
+enum RedOp { RED_SUM = 0, RED_MIN = 1, RED_MAX = 2 };
+bal_status finish_reduce_offset(Scene& S, int offset, int n, int slot, RedOp op, cudaStream_t st);
+inline bal_status finish_reduce(Scene& S, int n, int slot, RedOp op, cudaStream_t st) {
+  return finish_reduce_offset(S, 0, n, slot, op, st);
+}
+
+}  // namespace bal
