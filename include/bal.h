@@ -21,6 +21,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define BAL_API __attribute__((visibility("default")))
+#else
+#define BAL_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -161,37 +167,37 @@ typedef struct {
 } bal_step_info;
 
 /* ---- lifetime ------------------------------------------------------------ */
-const char* bal_last_error(void);
-void bal_default_params(bal_params* out);
+BAL_API const char* bal_last_error(void);
+BAL_API void bal_default_params(bal_params* out);
 
 /* Copies the topology, precomputes D_m^{-1}, rest volumes, Lame parameters and
  * lumped masses (Sec. 3.1), and builds the static lower BSR pattern with its
  * element-to-slot map (Sec. 5.1, App. C). Allocates the scene's device
  * buffers on the current device. */
-bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params,
+BAL_API bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params,
                             bal_scene** out);
-bal_status bal_destroy_scene(bal_scene* scene);
-bal_status bal_set_params(bal_scene* scene, const bal_params* params);
-bal_status bal_get_params(const bal_scene* scene, bal_params* out);
+BAL_API bal_status bal_destroy_scene(bal_scene* scene);
+BAL_API bal_status bal_set_params(bal_scene* scene, const bal_params* params);
+BAL_API bal_status bal_get_params(const bal_scene* scene, bal_params* out);
 /* Host copies of the static pattern: row_ptr [n_verts+1], col [nnz_L]; either
  * may be NULL to query nnz only. */
-bal_status bal_static_pattern(const bal_scene* scene, int64_t* nnz_L, int32_t* row_ptr,
+BAL_API bal_status bal_static_pattern(const bal_scene* scene, int64_t* nnz_L, int32_t* row_ptr,
                               int32_t* col);
 /* Lumped masses [n_verts] (host out). */
-bal_status bal_get_mass(const bal_scene* scene, double* mass_host);
+BAL_API bal_status bal_get_mass(const bal_scene* scene, double* mass_host);
 
 /* ---- time step state ------------------------------------------------------ */
 /* Starts a time step from (x_t, v_t) (device): y = x_t + h v_t + h^2 g
  * (Sec. 3.1), A at x_t, sigma0 (Sec. 3.4), mu = 0, A' empty. */
-bal_status bal_step_begin(bal_scene* scene, const double* x_t, const double* v_t,
+BAL_API bal_status bal_step_begin(bal_scene* scene, const double* x_t, const double* v_t,
                           void* stream);
 /* AL state of the current step. ap_keys / ap_mu may be NULL to query n_ap;
  * otherwise they must hold `capacity` entries. */
-bal_status bal_get_al_state(const bal_scene* scene, bal_al_state* out, int64_t capacity);
+BAL_API bal_status bal_get_al_state(const bal_scene* scene, bal_al_state* out, int64_t capacity);
 /* Replaces sigma, sigma0, dmin_prev and A' (host keys sorted ascending). */
-bal_status bal_set_al_state(bal_scene* scene, const bal_al_state* in);
+BAL_API bal_status bal_set_al_state(bal_scene* scene, const bal_al_state* in);
 /* Inertia target y of the current step into y_out (device). */
-bal_status bal_get_y(const bal_scene* scene, double* y_out, void* stream);
+BAL_API bal_status bal_get_y(const bal_scene* scene, double* y_out, void* stream);
 
 /* ---- hot-path calls --------------------------------------------------------- */
 /* Assembles at x (device) the gradient e = grad L_sigma (Eq. aug-lag; pinned
@@ -201,27 +207,27 @@ bal_status bal_get_y(const bal_scene* scene, double* y_out, void* stream);
  * found at x and A', mu, sigma from the current step state; s_i evaluated at x
  * (Sec. 3.2.2). Pinned rows and columns are eliminated with diagonal m/h^2
  * (App. C). Fills *view if non-NULL. */
-bal_status bal_assemble_hessian(bal_scene* scene, const double* x, double* grad_out,
+BAL_API bal_status bal_assemble_hessian(bal_scene* scene, const double* x, double* grad_out,
                                 bal_bsr_view* view, void* stream);
 /* y = H v with the last assembled H (Sec. 5.1 SpMV; device in/out). */
-bal_status bal_spmv(bal_scene* scene, const double* v, double* y, void* stream);
+BAL_API bal_status bal_spmv(bal_scene* scene, const double* v, double* y, void* stream);
 /* Solves H sol = rhs with block-Jacobi PCG (Sec. 4.2, App. B), optionally
  * warm-started by the stiffness-grouped subdomain solve (Sec. 4.2.2), or in
  * FP32 with FP64 iterative refinement, from sol_inout. Stops at
  * ||r_k|| <= rel_tol ||r_0||, when the residual reaches no new minimum in
  * pcg_stall_window iterations, or at max_iter. */
-bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* sol_inout,
+BAL_API bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* sol_inout,
                          double rel_tol, int32_t max_iter, bal_solve_info* info,
                          void* stream);
 /* L_sigma at x with A(x) and the step's A' state (host out). */
-bal_status bal_energy(bal_scene* scene, const double* x, double* energy_out, void* stream);
+BAL_API bal_status bal_energy(bal_scene* scene, const double* x, double* energy_out, void* stream);
 /* One Alg. 1 iteration l on x_inout (device): dual update of the previous
  * iteration, A, A' rule, gradient and convergence test, assembly, PCG, step
  * bound, backtracking line search (Sec. 5.2 memory cap). */
-bal_status bal_newton_step(bal_scene* scene, double* x_inout, bal_newton_info* info,
+BAL_API bal_status bal_newton_step(bal_scene* scene, double* x_inout, bal_newton_info* info,
                            void* stream);
 /* Full time step: bal_step_begin + Alg. 1 loop + v = (x - x_t)/h (Sec. 3.1). */
-bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_inout,
+BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_inout,
                          bal_step_info* info, void* stream);
 
 #ifdef __cplusplus

@@ -1,0 +1,276 @@
+// Broad phase: uniform-grid hash over the boundary primitives. Produces every
+// point-triangle and edge-edge pair (not sharing a vertex) whose primitives'
+// axis-aligned boxes come within r of each other -- a superset of the pairs
+// with distance below r -- each pair exactly once, sorted by pair key.
+//
+// PT: triangles are inserted, with their box inflated by r, into every cell the
+// box overlaps; each surface vertex scans the one cell that contains it.
+// EE: edges are inserted the same way; each edge scans the cells overlapped by
+// its own (non-inflated) box and keeps a pair (e, f), f > e, only in the cell
+// that contains the lower corner of box(e) n inflated-box(f), so a pair found
+// in several cells is reported once.
+// (The paper's broad phase is an LBVH, Sec. 5.3; the grid is this build's.)
+#include <cub/cub.cuh>
+
+#include "scene.cuh"
+
+namespace bal {
+
+namespace {
+
+constexpr int kOff = 1 << 20;
+constexpr int64_t kMaxCellsPerPrim = 1 << 20;
+
+struct Grid {
+  double inv_c;
+  double r;
+};
+
+__device__ inline int cell_of(double v, double inv_c) {
+  double f = floor(v * inv_c);
+  f = fmin(fmax(f, -(double)(kOff - 1)), (double)(kOff - 1));
+  return (int)f;
+}
+__device__ inline uint64_t cell_key(int ix, int iy, int iz) {
+  return ((uint64_t)(ix + kOff) << 42) | ((uint64_t)(iy + kOff) << 21) | (uint64_t)(iz + kOff);
+}
+
+struct Box {
+  d3 lo, hi;
+};
+__device__ inline Box prim_box(const double* x, const int* v, int nv) {
+  Box b;
+  b.lo = ld3(x, v[0]);
+  b.hi = b.lo;
+  for (int k = 1; k < nv; ++k) {
+    const d3 p = ld3(x, v[k]);
+    b.lo = d3{fmin(b.lo.x, p.x), fmin(b.lo.y, p.y), fmin(b.lo.z, p.z)};
+    b.hi = d3{fmax(b.hi.x, p.x), fmax(b.hi.y, p.y), fmax(b.hi.z, p.z)};
+  }
+  return b;
+}
+__device__ inline Box inflate(Box b, double r) {
+  return Box{d3{b.lo.x - r, b.lo.y - r, b.lo.z - r}, d3{b.hi.x + r, b.hi.y + r, b.hi.z + r}};
+}
+__device__ inline bool overlap(const Box& a, const Box& b) {
+  return a.lo.x <= b.hi.x && b.lo.x <= a.hi.x && a.lo.y <= b.hi.y && b.lo.y <= a.hi.y &&
+         a.lo.z <= b.hi.z && b.lo.z <= a.hi.z;
+}
+
+__device__ inline void prim_verts(const Dev& S, int kind, int id, int v[3], int& nv) {
+  if (kind == 0) {
+    v[0] = S.tris[3 * (int64_t)id];
+    v[1] = S.tris[3 * (int64_t)id + 1];
+    v[2] = S.tris[3 * (int64_t)id + 2];
+    nv = 3;
+  } else {
+    v[0] = S.edges[2 * (int64_t)id];
+    v[1] = S.edges[2 * (int64_t)id + 1];
+    nv = 2;
+  }
+}
+
+// number of cells of each inflated primitive box (kind 0 = triangles, 1 = edges)
+__global__ void k_count_cells(Dev S, const double* __restrict__ x, int kind, int n, Grid G,
+                              int64_t* __restrict__ count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int v[3], nv;
+    prim_verts(S, kind, i, v, nv);
+    const Box b = inflate(prim_box(x, v, nv), G.r);
+    const int64_t c = (int64_t)(cell_of(b.hi.x, G.inv_c) - cell_of(b.lo.x, G.inv_c) + 1) *
+                      (cell_of(b.hi.y, G.inv_c) - cell_of(b.lo.y, G.inv_c) + 1) *
+                      (cell_of(b.hi.z, G.inv_c) - cell_of(b.lo.z, G.inv_c) + 1);
+    count[i] = c > kMaxCellsPerPrim ? kMaxCellsPerPrim : c;
+  }
+}
+
+__global__ void k_fill_cells(Dev S, const double* __restrict__ x, int kind, int n, Grid G,
+                             const int64_t* __restrict__ offs, uint64_t* __restrict__ cells,
+                             int32_t* __restrict__ ids) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int v[3], nv;
+    prim_verts(S, kind, i, v, nv);
+    const Box b = inflate(prim_box(x, v, nv), G.r);
+    const int x0 = cell_of(b.lo.x, G.inv_c), x1 = cell_of(b.hi.x, G.inv_c);
+    const int y0 = cell_of(b.lo.y, G.inv_c), y1 = cell_of(b.hi.y, G.inv_c);
+    const int z0 = cell_of(b.lo.z, G.inv_c), z1 = cell_of(b.hi.z, G.inv_c);
+    int64_t o = offs[i];
+    const int64_t end = offs[i + 1];
+    for (int ix = x0; ix <= x1; ++ix)
+      for (int iy = y0; iy <= y1; ++iy)
+        for (int iz = z0; iz <= z1; ++iz) {
+          if (o >= end) return;
+          cells[o] = cell_key(ix, iy, iz);
+          ids[o] = i;
+          ++o;
+        }
+  }
+}
+
+__device__ inline int64_t lower_bound(const uint64_t* a, int64_t n, uint64_t k) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < k) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ inline void emit(uint64_t* out, unsigned long long* counter, int64_t cap, uint64_t key) {
+  const unsigned long long idx = atomicAdd(counter, 1ull);
+  if ((int64_t)idx < cap) out[idx] = key;
+}
+
+__global__ void k_pt_query(Dev S, const double* __restrict__ x, Grid G,
+                           const uint64_t* __restrict__ cells, const int32_t* __restrict__ ids,
+                           int64_t ncell, uint64_t* out, unsigned long long* counter, int64_t cap) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nsv; i += gridDim.x * blockDim.x) {
+    const int v = S.surf[i];
+    const d3 p = ld3(x, v);
+    const uint64_t key = cell_key(cell_of(p.x, G.inv_c), cell_of(p.y, G.inv_c), cell_of(p.z, G.inv_c));
+    for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
+      const int t = ids[k];
+      int tv[3], nv;
+      prim_verts(S, 0, t, tv, nv);
+      if (tv[0] == v || tv[1] == v || tv[2] == v) continue;
+      const Box b = inflate(prim_box(x, tv, 3), G.r);
+      if (p.x < b.lo.x || p.x > b.hi.x || p.y < b.lo.y || p.y > b.hi.y || p.z < b.lo.z ||
+          p.z > b.hi.z)
+        continue;
+      emit(out, counter, cap, pair_key(0, (uint32_t)v, (uint32_t)t));
+    }
+  }
+}
+
+__global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
+                           const uint64_t* __restrict__ cells, const int32_t* __restrict__ ids,
+                           int64_t ncell, uint64_t* out, unsigned long long* counter, int64_t cap) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.ne; e += gridDim.x * blockDim.x) {
+    int ev[3], nv;
+    prim_verts(S, 1, e, ev, nv);
+    const Box be = prim_box(x, ev, 2);
+    const int x0 = cell_of(be.lo.x, G.inv_c), x1 = cell_of(be.hi.x, G.inv_c);
+    const int y0 = cell_of(be.lo.y, G.inv_c), y1 = cell_of(be.hi.y, G.inv_c);
+    const int z0 = cell_of(be.lo.z, G.inv_c), z1 = cell_of(be.hi.z, G.inv_c);
+    for (int ix = x0; ix <= x1; ++ix)
+      for (int iy = y0; iy <= y1; ++iy)
+        for (int iz = z0; iz <= z1; ++iz) {
+          const uint64_t key = cell_key(ix, iy, iz);
+          for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
+            const int f = ids[k];
+            if (f <= e) continue;
+            int fv[3];
+            prim_verts(S, 1, f, fv, nv);
+            if (fv[0] == ev[0] || fv[0] == ev[1] || fv[1] == ev[0] || fv[1] == ev[1]) continue;
+            const Box bf = inflate(prim_box(x, fv, 2), G.r);
+            if (!overlap(be, bf)) continue;
+            const d3 lo = d3{fmax(be.lo.x, bf.lo.x), fmax(be.lo.y, bf.lo.y), fmax(be.lo.z, bf.lo.z)};
+            if (cell_of(lo.x, G.inv_c) != ix || cell_of(lo.y, G.inv_c) != iy ||
+                cell_of(lo.z, G.inv_c) != iz)
+              continue;
+            emit(out, counter, cap, pair_key(1, (uint32_t)e, (uint32_t)f));
+          }
+        }
+  }
+}
+
+// Builds the sorted (cell, primitive) list of one primitive kind.
+bal_status build_cells(Scene& S, const double* x, int kind, int n, Grid G, int64_t* ncell,
+                       uint64_t** cells_out, int32_t** ids_out, cudaStream_t st) {
+  *ncell = 0;
+  if (n == 0) return BAL_OK;
+  BAL_TRY(buf_reserve(S.bp_count, sizeof(int64_t) * (n + 1)));
+  BAL_TRY(buf_reserve(S.bp_offs, sizeof(int64_t) * (n + 1)));
+  int64_t* cnt = S.bp_count.as<int64_t>();
+  int64_t* offs = S.bp_offs.as<int64_t>();
+  k_count_cells<<<grid_for(n), kThreads, 0, st>>>(S.d, x, kind, n, G, cnt);
+  BAL_LAUNCH_CHECK();
+  BAL_CUDA(cudaMemsetAsync(cnt + n, 0, sizeof(int64_t), st));
+  size_t tmp = 0;
+  BAL_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, offs, n + 1, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceScan::ExclusiveSum(S.cub_tmp.p, tmp, cnt, offs, n + 1, st));
+  int64_t total = 0;
+  BAL_CUDA(cudaMemcpyAsync(&total, offs + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  if (total > (int64_t)1 << 31) {
+    set_error("broad phase: %lld (cell, primitive) entries; query radius too large", (long long)total);
+    return BAL_ERR_CAPACITY;
+  }
+  BAL_TRY(buf_reserve(S.bp_cells, sizeof(uint64_t) * total));
+  BAL_TRY(buf_reserve(S.bp_cells_alt, sizeof(uint64_t) * total));
+  BAL_TRY(buf_reserve(S.bp_ids, sizeof(int32_t) * total));
+  BAL_TRY(buf_reserve(S.bp_ids_alt, sizeof(int32_t) * total));
+  k_fill_cells<<<grid_for(n), kThreads, 0, st>>>(S.d, x, kind, n, G, offs,
+                                                 S.bp_cells.as<uint64_t>(), S.bp_ids.as<int32_t>());
+  BAL_LAUNCH_CHECK();
+  cub::DoubleBuffer<uint64_t> dk(S.bp_cells.as<uint64_t>(), S.bp_cells_alt.as<uint64_t>());
+  cub::DoubleBuffer<int32_t> dv(S.bp_ids.as<int32_t>(), S.bp_ids_alt.as<int32_t>());
+  tmp = 0;
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, (int64_t)total, 0, 63, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, (int64_t)total, 0, 63, st));
+  *ncell = total;
+  *cells_out = dk.Current();
+  *ids_out = dv.Current();
+  return BAL_OK;
+}
+
+}  // namespace
+
+bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt, int64_t* n,
+                           cudaStream_t st) {
+  Grid G;
+  const double c = 2.0 * r + 1.5 * S.mean_edge;
+  G.inv_c = 1.0 / c;
+  G.r = r;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(S.scal + 63);
+  int64_t cap = (int64_t)(out.cap / sizeof(uint64_t));
+  if (cap < 1024) {
+    BAL_TRY(buf_reserve(out, sizeof(uint64_t) * 1024));
+    cap = 1024;
+  }
+  unsigned long long found = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    BAL_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    // PT: triangles in cells, vertices query
+    int64_t ncell = 0;
+    uint64_t* cells = nullptr;
+    int32_t* ids = nullptr;
+    BAL_TRY(build_cells(S, x, 0, S.d.nf, G, &ncell, &cells, &ids, st));
+    if (ncell > 0 && S.d.nsv > 0) {
+      k_pt_query<<<grid_for(S.d.nsv), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
+                                                          out.as<uint64_t>(), counter, cap);
+      BAL_LAUNCH_CHECK();
+    }
+    BAL_TRY(build_cells(S, x, 1, S.d.ne, G, &ncell, &cells, &ids, st));
+    if (ncell > 0) {
+      k_ee_query<<<grid_for(S.d.ne), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
+                                                         out.as<uint64_t>(), counter, cap);
+      BAL_LAUNCH_CHECK();
+    }
+    BAL_CUDA(cudaMemcpyAsync(&found, counter, sizeof(found), cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+    if ((int64_t)found <= cap) break;
+    if ((int64_t)found > S.pair_limit) {
+      set_error("broad phase: %llu candidate pairs exceed pair_limit %lld", found,
+                (long long)S.pair_limit);
+      return BAL_ERR_CAPACITY;
+    }
+    cap = (int64_t)(found + found / 4 + 1024);
+    BAL_TRY(buf_reserve(out, sizeof(uint64_t) * cap));
+  }
+  *n = (int64_t)found;
+  if (found > 1) {
+    BAL_TRY(buf_reserve(alt, sizeof(uint64_t) * found));
+    cub::DoubleBuffer<uint64_t> dk(out.as<uint64_t>(), alt.as<uint64_t>());
+    size_t tmp = 0;
+    BAL_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, dk, (int64_t)found, 0, 64, st));
+    BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+    BAL_CUDA(cub::DeviceRadixSort::SortKeys(S.cub_tmp.p, tmp, dk, (int64_t)found, 0, 64, st));
+    if (dk.Current() != out.as<uint64_t>()) std::swap(out, alt);
+  }
+  return BAL_OK;
+}
+
+}  // namespace bal

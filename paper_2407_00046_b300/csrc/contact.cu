@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restrict__ x,
-                                                   const double* __restrict__ pn,
+                                                   const double* __restrict__ dir,
                                                    const uint64_t* __restrict__ cand, int64_t nc,
                                                    double eta, double* partials) {
   double amin = 1.0;
@@ -538,11 +538,17 @@ __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restri
     Region R;
     const uint64_t key = cand[i];
     const double d = pair_distance(S, x, key, v, X, R);
-    double Dl;
-    if (key_kind(key) == 0)
-      Dl = pn[v[0]] + fmax(pn[v[1]], fmax(pn[v[2]], pn[v[3]]));
-    else
-      Dl = fmax(pn[v[0]], pn[v[1]]) + fmax(pn[v[2]], pn[v[3]]);
+    // largest relative node displacement across the pair
+    d3 P[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) P[a] = ld3(dir, v[a]);
+    const int na = key_kind(key) == 0 ? 1 : 2;
+    double Dl = 0.0;
+    for (int a = 0; a < na; ++a)
+      for (int b = na; b < 4; ++b) {
+        const d3 w = P[a] - P[b];
+        Dl = fmax(Dl, sqrt(dot(w, w)));
+      }
     if (eta * d < Dl) amin = fmin(amin, eta * d / Dl);
   }
   amin = block_min<double, NT>(amin, 1.0);
@@ -610,11 +616,11 @@ bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand
   return BAL_OK;
 }
 
-bal_status launch_step_bound(Scene& S, const double* x, const double* pnorm,
+bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
                              const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st) {
   constexpr int NT = 256;
   const int nblk = 2 * kNumSM;
-  k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, pnorm, cand, ncand, S.prm.step_bound, S.partials);
+  k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound, S.partials);
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);
 }

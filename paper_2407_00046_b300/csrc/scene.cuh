@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -132,8 +133,9 @@ bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool he
 // Writes S.scal[slot] = contact energy, S.scal[slot+1] = count of d < dhat over keys.
 bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand, int64_t ncand,
                                  int slot, cudaStream_t st);
-// min over candidates of step_bound*d/Delta (where step_bound*d < Delta) -> S.scal[slot].
-bal_status launch_step_bound(Scene& S, const double* x, const double* pnorm,
+// min over candidates of step_bound*d/Delta_i (where step_bound*d < Delta_i), with
+// Delta_i = max |p_a - p_b| over a node of each primitive -> S.scal[slot].
+bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
                              const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st);
 // A' dual update: s_i, mu_i += sigma b(d_i, dhat + s_i) for the device A' list.
 bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t st);
@@ -148,8 +150,19 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
 bal_status launch_dinv(Scene& S, cudaStream_t st);
 bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
+// S.scal[8] = ||b - y||^2, S.scal[9] = ||b||^2
+bal_status launch_residual_norm(Scene& S, const double* b, const double* y, cudaStream_t st);
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
                      bal_solve_info* info, cudaStream_t st);
+
+// ---- vec.cu ----------------------------------------------------------------------
+bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y, cudaStream_t st);
+// out = y + a x over n doubles
+bal_status launch_axpy(Scene& S, int64_t n, double a, const double* x, const double* y, double* out,
+                       cudaStream_t st);
+bal_status launch_dot(Scene& S, int64_t n, const double* a, const double* b, int slot, cudaStream_t st);
+// S.scal[slot] = max over surface vertices of |d_v|
+bal_status launch_surf_max_norm(Scene& S, const double* d, int slot, cudaStream_t st);
 
 // ---- reductions helper (matrix.cu) -----------------------------------------------
 // S.scal[slot] = sum / min / max of partials[0..n)
