@@ -209,6 +209,13 @@ BAL_API bal_status bal_get_y(const bal_scene* scene, double* y_out, void* stream
  * (App. C). Fills *view if non-NULL. */
 BAL_API bal_status bal_assemble_hessian(bal_scene* scene, const double* x, double* grad_out,
                                 bal_bsr_view* view, void* stream);
+/* Copies the last assembled Hessian into caller-owned DEVICE buffers (any may
+ * be NULL): D [n_verts*9], L values [nnz_L*9], contact rows/cols [nnz_C],
+ * contact values [nnz_C*9], Lambda [n_verts*3]. Sizes are those reported in
+ * bal_bsr_view by the assemble call. */
+BAL_API bal_status bal_copy_hessian(bal_scene* scene, double* D_out, double* L_val_out,
+                                    int32_t* C_row_out, int32_t* C_col_out, double* C_val_out,
+                                    double* Lambda_out, void* stream);
 /* y = H v with the last assembled H (Sec. 5.1 SpMV; device in/out). */
 BAL_API bal_status bal_spmv(bal_scene* scene, const double* v, double* y, void* stream);
 /* Solves H sol = rhs with block-Jacobi PCG (Sec. 4.2, App. B), optionally

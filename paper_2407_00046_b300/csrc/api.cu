@@ -471,7 +471,9 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   *out = nullptr;
   if (desc->n_verts <= 0 || desc->n_tets < 0 || desc->n_tris < 0 || desc->n_edges < 0 ||
       desc->n_surf_verts < 0 || !desc->X || (desc->n_tets > 0 && !desc->tets) ||
-      !(desc->h > 0) || !(desc->dhat > 0)) {
+      !(desc->h > 0) || !(desc->dhat > 0) || !desc->E || !desc->nu || !desc->rho ||
+      !desc->pinned || (desc->n_tris > 0 && !desc->tris) || (desc->n_edges > 0 && !desc->edges) ||
+      (desc->n_surf_verts > 0 && !desc->surf_verts)) {
     set_error("bal_create_scene: invalid sizes, pointers, h or dhat");
     return BAL_ERR_ARG;
   }
@@ -809,6 +811,28 @@ bal_status bal_assemble_hessian(bal_scene* sc, const double* x, double* grad_out
     view->C_val = S.C_val.as<double>();
     view->Lambda = S.d.Lambda;
   }
+  return BAL_OK;
+}
+
+bal_status bal_copy_hessian(bal_scene* sc, double* D_out, double* L_out, int32_t* Cr, int32_t* Cc,
+                            double* Cv, double* Lam, void* stream) {
+  BAL_TRY(check_scene(sc));
+  Scene& S = sc->S;
+  if (!S.assembled) {
+    set_error("bal_copy_hessian: no assembled Hessian");
+    return BAL_ERR_STATE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto d2d = cudaMemcpyDeviceToDevice;
+  if (D_out) BAL_CUDA(cudaMemcpyAsync(D_out, S.d.D, sizeof(double) * 9 * S.d.nv, d2d, st));
+  if (L_out && S.d.nnzL) BAL_CUDA(cudaMemcpyAsync(L_out, S.d.Lval, sizeof(double) * 9 * S.d.nnzL, d2d, st));
+  if (S.nnzC) {
+    if (Cr) BAL_CUDA(cudaMemcpyAsync(Cr, S.C_row.p, sizeof(int32_t) * S.nnzC, d2d, st));
+    if (Cc) BAL_CUDA(cudaMemcpyAsync(Cc, S.C_col.p, sizeof(int32_t) * S.nnzC, d2d, st));
+    if (Cv) BAL_CUDA(cudaMemcpyAsync(Cv, S.C_val.p, sizeof(double) * 9 * S.nnzC, d2d, st));
+  }
+  if (Lam) BAL_CUDA(cudaMemcpyAsync(Lam, S.d.Lambda, sizeof(double) * 3 * S.d.nv, d2d, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
   return BAL_OK;
 }
 

@@ -1,0 +1,167 @@
+"""GPU parity: every hot-path call of libbal through the C ABI against the FP64
+oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bal as obal  # noqa: E402
+from oracle import system  # noqa: E402
+from paper_2407_00046_b300 import bal, scenes  # noqa: E402
+
+from gpu_common import close_cubes, gpu_hessian, oracle_state  # noqa: E402
+
+DEV = "cuda"
+HESS_TOL = 1e-10      # |H_gpu - H_oracle|_max / |H_oracle|_max
+GRAD_TOL = 1e-10
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+@pytest.fixture(scope="module")
+def contact_case():
+    sc = close_cubes(n=3)
+    rng = np.random.default_rng(7)
+    x = sc.X + 1e-4 * rng.normal(size=sc.X.shape) * (sc.pinned == 0)[:, None]
+    S = bal.Scene(sc, bal.default_params())
+    S.step_begin(T(sc.X), T(sc.V0))
+    return sc, S, x
+
+
+def test_sigma0_matches_oracle(contact_case):
+    sc, S, _ = contact_case
+    m = system.make_model(sc)
+    y = system.inertia_target(m, sc.X, sc.V0)
+    keys, _ = obal.active_pairs(m, sc.X)
+    assert len(keys) > 0
+    s0 = obal.initial_sigma(m, sc.X, y, keys)
+    al = S.get_al_state()
+    assert al["sigma0"] == pytest.approx(s0, rel=1e-10)
+
+
+@pytest.mark.parametrize("with_ap", [False, True])
+def test_assembly_matches_oracle(contact_case, with_ap):
+    sc, S, x = contact_case
+    sigma = 7.5
+    ap = {}
+    if with_ap:
+        m = system.make_model(sc)
+        keys, _ = obal.active_pairs(m, x)
+        ap = {k: 0.05 * (i % 5) for i, k in enumerate(keys[::4])}
+    S.set_al_state(sigma, sigma, [bal.pair_key(*k) for k in sorted(ap)], [ap[k] for k in sorted(ap)])
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    view = S.assemble_hessian(T(x), g)
+    Hg, lam_g, _ = gpu_hessian(S, view)
+    m, y, ps = oracle_state(sc, x, sigma, ap)
+    g_or = system.gradient(m, x, y, ps, sigma).ravel()
+    H_or, lam_or = system.hessian(m, x, y, ps, sigma, with_lambda=True)
+    gerr = np.abs(g.cpu().numpy() - g_or).max() / np.abs(g_or).max()
+    herr = np.abs((Hg - H_or).toarray()).max() / np.abs(H_or.toarray()).max()
+    lerr = np.abs(lam_g - lam_or).max() / np.abs(lam_or).max()
+    assert gerr < GRAD_TOL, gerr
+    assert herr < HESS_TOL, herr
+    assert lerr < HESS_TOL, lerr
+    assert view["nnz_C"] > 0
+
+
+def test_spmv_matches_oracle(contact_case):
+    sc, S, x = contact_case
+    S.set_al_state(3.0, 3.0)
+    view = S.assemble_hessian(T(x))
+    m, y, ps = oracle_state(sc, x, 3.0)
+    H_or = system.hessian(m, x, y, ps, 3.0)
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=3 * sc.n_verts)
+    yv = torch.empty_like(T(v))
+    S.spmv(T(v), yv)
+    ref = H_or @ v
+    assert np.abs(yv.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-11
+    assert view["nnz_L"] > 0
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+def test_pcg_residual_checked_by_oracle(contact_case, tol):
+    sc, S, x = contact_case
+    S.set_al_state(3.0, 3.0)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    S.assemble_hessian(T(x), g)
+    m, y, ps = oracle_state(sc, x, 3.0)
+    H_or = system.hessian(m, x, y, ps, 3.0)
+    b = -g
+    sol = torch.zeros_like(b)
+    info = S.pcg_solve(b, sol, tol, 5000)
+    bn = b.cpu().numpy()
+    res = np.linalg.norm(bn - H_or @ sol.cpu().numpy()) / np.linalg.norm(bn)
+    assert info["converged"] == 1
+    assert res <= 1.05 * tol, (res, info)
+    assert abs(info["rel_residual"] - res) <= 1e-3 * res + 1e-15
+
+
+def test_pcg_edge_cases(contact_case):
+    sc, S, x = contact_case
+    S.set_al_state(3.0, 3.0)
+    S.assemble_hessian(T(x))
+    z = torch.zeros(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    sol = torch.zeros_like(z)
+    info = S.pcg_solve(z, sol, 1e-8, 100)          # zero right-hand side
+    assert info["iters"] == 0 and float(sol.abs().max()) == 0.0
+    b = torch.ones_like(z)
+    info = S.pcg_solve(b, sol, 1e-8, 0)            # zero iteration cap
+    assert info["iters"] == 0
+
+
+def test_energy_matches_oracle(contact_case):
+    sc, S, x = contact_case
+    S.set_al_state(4.0, 4.0)
+    e = S.energy(T(x))
+    m, y, ps = oracle_state(sc, x, 4.0)
+    e_or = system.energy(m, x, y, ps, 4.0)
+    assert e == pytest.approx(e_or, rel=1e-12)
+
+
+def test_free_flight_is_exact():
+    X, Tt = scenes.lattice_box(3, 3, 3, (0.1, 0.1, 0.1))
+    sc = scenes.merge_bodies("free", [dict(X=X, tets=Tt, E=1e5, V0=np.array([0.1, 0.2, -0.3]))])
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-12, pcg_tol=1e-14))
+    x, v = T(sc.X), T(sc.V0)
+    S.step_begin(x, v)
+    y = torch.empty_like(x)
+    S.get_y(y)
+    info = S.time_step(x, v)
+    assert info["converged"] == 1
+    assert float((x - y).abs().max()) < 1e-13
+
+
+def _trajectory(sc, steps, newton_tol=1e-8):
+    S = bal.Scene(sc, bal.default_params(newton_tol=newton_tol, pcg_tol=1e-12, pcg_max_iter=20000))
+    m = system.make_model(sc)
+    x, v = T(sc.X), T(sc.V0)
+    xo, vo = sc.X.copy(), sc.V0.copy()
+    out = []
+    for _ in range(steps):
+        info = S.time_step(x, v)
+        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=newton_tol))
+        out.append((np.abs(x.cpu().numpy() - xo).max(), info, io))
+    return out
+
+
+def test_time_step_trajectory_small():
+    sc = close_cubes(n=2, gap=5e-4)
+    for dx, info, io in _trajectory(sc, 3):
+        assert info["converged"] == 1 and io["converged"]
+        assert dx < 1e-8, (dx, info, io["iters"])
+
+
+def test_newton_step_counts_match_oracle():
+    sc = close_cubes(n=2, gap=3e-4)
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12))
+    x, v = T(sc.X), T(sc.V0)
+    S.step_begin(x, v)
+    info = S.newton_step(x)
+    m = system.make_model(sc)
+    keys, _ = obal.active_pairs(m, sc.X)
+    assert info["n_active"] == len(keys) and info["n_active"] > 0
+    assert info["alpha"] > 0
