@@ -1,0 +1,350 @@
+"""Benchmark of the BAL inexact Newton-PCG time step on one B300.
+
+Workload (default): the heterogeneous net scene -- an interlocked torus-link
+chain net (E = 1 GPa, border links pinned) under four spiked spherical shells
+(E = 5e5 Pa) dropped from 2 cm, ~1.77M tets, h = 1/30 s, dhat = 1e-3 m,
+synthetic and seeded (it stands in for the paper's "Puffer Balls on Nets",
+Table 1). A step is one full time step (Algorithm 1 until convergence: contact
+detection, assembly, PCG solves, line searches). W warm-up steps (the shells
+reach the net), then K timed steps.
+
+Prints one JSON line. value = PCG iterations per second over the timed steps
+(whole step time, all ranks); ms_per_step = wall time per time step. The
+matrix is larger than L2 at this size, so no L2 flush is inserted.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+Multi-GPU: independent replicas of the scene, one per rank (weak scaling; the
+path has no collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG iters/s and ms per time step at 1.7M tets; BSR SpMV % of HBM peak"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            return out
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = float(rows[0][2])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip() == "Active":
+                    seen.add(name)
+        out["reasons"] = sorted(seen)
+        out["samples"] = len(rows)
+        return out
+
+
+def spmv_bytes(nv, nnzL, nnzC, p=8):
+    """Algorithmic bytes of one symmetric SpMV: D, L and C blocks, their column
+    indices, the row pointer, and one read of v plus one write of y."""
+    return (nv + nnzL + nnzC) * 9 * p + (nnzL + nnzC) * 4 + (nv + 1) * 4 + 2 * 3 * nv * p
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2407_00046_b300 import bal, build, scenes
+
+    build.build(force=False, verbose=False)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    sc = scenes.scene_by_name(args.scene)
+    params = bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
+                                newton_max_iter=args.newton_max,
+                                precision=bal.PREC_MIXED if args.precision == "mixed" else bal.PREC_FP64)
+    S = bal.Scene(sc, params, pair_capacity=1 << 22)
+    stream = torch.cuda.current_stream()
+    x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
+    v = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
+    log = []
+    for _ in range(args.warmup):
+        log.append(S.time_step(x, v, check=False))
+    x0, v0 = x.clone(), v.clone()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed = []
+    with Clocks(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            timed.append(S.time_step(x, v, check=False))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    pcg_iters = sum(t["pcg_iters_total"] for t in timed)
+    newton = sum(t["newton_iters"] for t in timed)
+
+    # end to end through the public API with host buffers (same steps again)
+    xh = x0.cpu().pin_memory()
+    vh = v0.cpu().pin_memory()
+    xd, vd = torch.empty_like(x0), torch.empty_like(v0)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    e2e_iters = 0
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        info = S.time_step(xd, vd, check=False)
+        e2e_iters += info["pcg_iters_total"]
+        xh.copy_(xd, non_blocking=True)
+        vh.copy_(vd, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+
+    # SpMV roofline on the last assembled Hessian (matrix > L2 at this size)
+    view = S.assemble_hessian(x)
+    nv, nnzL, nnzC = sc.n_verts, view["nnz_L"], view["nnz_C"]
+    vec = torch.randn(3 * nv, dtype=torch.float64, device=dev)
+    out = torch.empty_like(vec)
+    for _ in range(3):
+        S.spmv(vec, out)
+    reps = 50
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        S.spmv(vec, out)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / reps
+    byts = spmv_bytes(nv, nnzL, nnzC)
+    peak, peak_kind = peaks()
+    achieved = byts / (spmv_ms * 1e-3) / 1e9
+    # PCG-only iteration rate on the same system (fixed iteration count)
+    rhs = torch.randn(3 * nv, dtype=torch.float64, device=dev)
+    sol = torch.zeros_like(rhs)
+    S.set_params(pcg_stall_window=1 << 30)
+    S.pcg_solve(rhs, sol, 0.0, 10)
+    sol.zero_()
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    pi = S.pcg_solve(rhs, sol, 0.0, 200)
+    torch.cuda.synchronize()
+    pcg_only = pi["iters"] / (time.perf_counter() - p0)
+
+    # max over ranks
+    vals = torch.tensor([ms, e2e_ms, float(pcg_iters), float(e2e_iters)], dtype=torch.float64)
+    if world > 1:
+        t = vals.to(dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        ms, e2e_ms = float(mx[0]), float(mx[1])
+        pcg_iters, e2e_iters = float(sm[2]), float(sm[3])
+    if rank != 0:
+        return None
+    value = pcg_iters / (ms * 1e-3)
+    e2e_val = e2e_iters / (e2e_ms * 1e-3)
+    launches = sum(t["newton_iters"] for t in timed)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "PCG iter/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded procedural scene, no paper meshes)",
+        "config": {
+            "workload": f"{sc.name}: {sc.n_tets} tets, {sc.n_verts} verts, h=1/30 s, dhat=1e-3 m",
+            "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
+            "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol,
+            "precond": "block-Jacobi", "precision": args.precision,
+            "l2": "no flush: Hessian storage exceeds the 126 MB L2",
+            "parallelism": f"replicas x{world}",
+        },
+        "newton_iters_per_step": newton / max(args.steps, 1),
+        "pcg_iters_per_step": pcg_iters / max(args.steps, 1) / max(world, 1),
+        "pcg_only_iters_per_s": round(pcg_only, 1),
+        "max_active_pairs": max((t["max_active"] for t in timed), default=0),
+        "phase_ms_per_step": {k: round(sum(t[k] for t in timed) / max(args.steps, 1), 2)
+                              for k in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")},
+        "e2e": {"value": round(e2e_val, 2), "unit": "PCG iter/s",
+                "h2d_bytes_per_step": 2 * 3 * nv * 8, "d2h_bytes_per_step": 2 * 3 * nv * 8},
+        "roofline": {"kernel": "bal_spmv (diag + off-diagonal blocks, FP64)", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": None, "bytes_per_launch": byts, "ms_per_launch": round(spmv_ms, 4),
+                     "nnz_L": nnzL, "nnz_C": nnzC,
+                     "fp64_tflops": round(36.0 * (nnzL + nnzC) / (spmv_ms * 1e-3) / 1e12, 3)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "status": [t["status"] for t in timed],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, nv, nnzL, nnzC)
+    return line
+
+
+def cpu_baseline(args, nv_full, nnzL_full, nnzC_full, budget_s=15.0):
+    """The FP64 oracle timed on this host's cores on a bounded sample: oracle
+    assembly of a small chain-net scene and scipy CSR matvec of its Hessian,
+    scaled by stored blocks to one PCG iteration (SpMV + 3 vector passes) of the
+    full workload."""
+    from oracle import system
+    from paper_2407_00046_b300 import scenes
+    t0 = time.perf_counter()
+    sc = scenes.scene_by_name("chain_net_shells_small")
+    m = system.make_model(sc)
+    y = system.inertia_target(m, sc.X, sc.V0)
+    ta = time.perf_counter()
+    H = system.hessian(m, sc.X, y, system.empty_pairs(), 1.0)
+    t_asm = time.perf_counter() - ta
+    v = np.random.default_rng(0).normal(size=H.shape[0])
+    reps, tm = 0, time.perf_counter()
+    while time.perf_counter() - tm < min(5.0, budget_s):
+        H @ v
+        reps += 1
+    t_spmv = (time.perf_counter() - tm) / reps
+    stored_small = H.nnz
+    stored_full = 9 * (nv_full + 2 * (nnzL_full + nnzC_full))
+    w = np.random.default_rng(1).normal(size=3 * nv_full)
+    tv = time.perf_counter()
+    for _ in range(3):
+        w = w + 0.5 * w
+        float(w @ w)
+    t_vec = time.perf_counter() - tv
+    t_iter = t_spmv * stored_full / stored_small + t_vec
+    return {"value": round(1.0 / t_iter, 3), "unit": "PCG iter/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle assembly ({sc.n_tets} tets, {t_asm:.2f} s) and scipy CSR matvec "
+                       f"({stored_small} stored entries, {t_spmv * 1e3:.2f} ms) of a 3x3-ring "
+                       f"chain net with one shell, scaled to {stored_full} stored entries "
+                       f"+ 3 vector passes of the full scene; single thread"),
+            "seconds": round(time.perf_counter() - t0, 1)}
+
+
+def run_reference(args):
+    t0 = time.perf_counter()
+    from paper_2407_00046_b300 import scenes
+    sc = scenes.scene_by_name(args.scene)
+    # stored blocks of the full workload from its static pattern (contact part
+    # not included: the reference arm has no GPU assembly to report it)
+    pairs = set()
+    T = sc.tets.astype(np.int64)
+    for a in range(4):
+        for b in range(a + 1, 4):
+            lo, hi = np.minimum(T[:, a], T[:, b]), np.maximum(T[:, a], T[:, b])
+            pairs.update((hi * sc.n_verts + lo).tolist())
+    nnzL = len(pairs)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args, sc.n_verts, nnzL, 0, budget_s=2.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, sc.n_verts, nnzL, 0, budget_s=5.0))
+    ms = (time.perf_counter() - t0) * 1e3
+    value = statistics.median(v["value"] for v in vals)
+    return {
+        "metric": METRIC, "value": value, "unit": "PCG iter/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / max(args.steps, 1), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"{sc.name}: {sc.n_tets} tets", "scene": args.scene},
+        "cpu_baseline": vals[-1],
+        "e2e": {"value": value, "unit": "PCG iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scene", default="chain_net_shells")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--pcg-tol", type=float, default=1e-6)
+    ap.add_argument("--newton-tol", type=float, default=1e-4)
+    ap.add_argument("--newton-max", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
