@@ -240,7 +240,7 @@ def spiked_shell(radius: float, thickness: float, m: int, layers: int,
         ids = np.zeros((5, 3, 3), dtype=np.int64)
         ids[0] = base
         for k in range(1, 5):
-            taper = 1.0 - 0.2 * k
+            taper = 1.0 - 0.125 * k
             pos = centre + (bpos - centre) * taper + normal * (spike_len * k / 4)
             ids[k] = next_id + np.arange(9).reshape(3, 3)
             next_id += 9
@@ -397,8 +397,8 @@ def cube_on_slab(n_cube: int = 26, L: float = 0.1, slab_cells=(58, 10, 58),
     ], info=dict(target=target, cube_body=0, n_cube=n_cube, seed=seed))
 
 
-def chain_net_shells(nx: int = 9, nz: int = 10, R: float = 0.025, half: float = 0.003,
-                     e: float = 0.01, n_shells: int = 4, shell_radius: float = 0.10,
+def chain_net_shells(nx: int = 9, nz: int = 10, R: float = 0.035, half: float = 0.006,
+                     e: float = 0.014, n_shells: int = 4, shell_radius: float = 0.10,
                      shell_thick: float = 0.01, shell_m: int = 32, shell_layers: int = 4,
                      n_spikes: int = 64, spike_len: float = 0.02, drop_gap: float = 0.02,
                      seed: int = 3, E_net: float = 1e9, E_shell: float = 5e5,
@@ -409,7 +409,9 @@ def chain_net_shells(nx: int = 9, nz: int = 10, R: float = 0.025, half: float = 
     vertical connector rings: x-connectors (plane xy) between x-neighbours and
     z-connectors (plane yz) between z-neighbours. Each connector passes through
     the holes of its two flat rings at distance e from their centres, so the
-    links interlock without touching (clearance > 1 mm). Border flat rings are
+    links interlock without touching (clearance > 1 mm). The cross-section
+    (2*half, n_cross cells) keeps the surface cells well above dhat so that no
+    surface comes within dhat of itself at rest. Border flat rings are
     pinned. Shells (cubed sphere, outer radius shell_radius, thickness
     shell_thick, 6*m^2*layers hexes, plus tapered spikes) hang in a 2x2 grid
     drop_gap above the net."""
