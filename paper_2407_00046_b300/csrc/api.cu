@@ -358,11 +358,7 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   t0 = clk::now();
   bool extra_done = false;
   for (;;) {
-    BAL_TRY(launch_surf_max_norm(S, S.dir, 13, st));
-    double delta;
-    BAL_TRY(read_scalars(S, &delta, 13, 1, st));
-    const double r = dh + 2.0 * delta / S.prm.step_bound;
-    BAL_TRY(find_candidates(S, x, r, S.ls_cand, S.ls_cand_alt, &S.n_ls_cand, st));
+    BAL_TRY(find_candidates_motion(S, x, S.dir, S.ls_cand, S.ls_cand_alt, &S.n_ls_cand, st));
     I.n_candidates = S.n_ls_cand;
     double alpha = 1.0;
     if (S.n_ls_cand > 0) {
@@ -584,6 +580,36 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
       slot[6 * (size_t)t + k] = (int32_t)(2 * s + (transpose ? 1 : 0));
     }
   }
+  // bodies: connected components of the tet mesh (union-find)
+  std::vector<int32_t> parent(nv);
+  for (int i = 0; i < nv; ++i) parent[i] = i;
+  auto find = [&](int a) {
+    while (parent[a] != a) {
+      parent[a] = parent[parent[a]];
+      a = parent[a];
+    }
+    return a;
+  };
+  for (int t = 0; t < nt; ++t) {
+    const int* v = desc->tets + 4 * (int64_t)t;
+    for (int k = 1; k < 4; ++k) {
+      const int a = find(v[0]), b = find(v[k]);
+      if (a != b) parent[std::max(a, b)] = std::min(a, b);
+    }
+  }
+  std::vector<int32_t> body(nv), root_id(nv, -1);
+  std::vector<double> bcnt;
+  for (int i = 0; i < nv; ++i) {
+    const int r = find(i);
+    if (root_id[r] < 0) {
+      root_id[r] = (int32_t)bcnt.size();
+      bcnt.push_back(0.0);
+    }
+    body[i] = root_id[r];
+    bcnt[body[i]] += 1.0;
+  }
+  for (double& c : bcnt) c = 1.0 / c;
+  S.nbody = (int32_t)bcnt.size();
   // mean surface edge length at rest (grid cell size)
   double el = 0.0;
   for (int e = 0; e < desc->n_edges; ++e) {
@@ -614,6 +640,9 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dupload(S, &S.d.L_col, (const int32_t*)S.col_h.data(), S.col_h.size()));
   TRYC(dupload(S, &S.d.L_row, (const int32_t*)rows.data(), rows.size()));
   TRYC(dupload(S, &S.d.tet_slot, (const int32_t*)slot.data(), slot.size()));
+  TRYC(dupload(S, (const int32_t**)&S.body, (const int32_t*)body.data(), body.size()));
+  TRYC(dupload(S, (const double**)&S.body_inv_cnt, (const double*)bcnt.data(), bcnt.size()));
+  TRYC(dalloc(S, &S.bmean, 3 * (size_t)S.nbody));
   TRYC(dalloc(S, &S.d.D, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.d.Dinv, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.d.Lval, 9 * (size_t)S.d.nnzL));
@@ -902,6 +931,7 @@ bal_status bal_time_step(bal_scene* sc, double* x, double* v, bal_step_info* inf
   bal_status status = BAL_ERR_NOT_CONVERGED;
   for (int l = 0; l < S.prm.newton_max_iter; ++l) {
     bal_newton_info ni;
+    std::memset(&ni, 0, sizeof(ni));
     const bal_status s = newton_iteration(S, x, &ni, st);
     I.ms_assemble += ni.ms_assemble;
     I.ms_solve += ni.ms_solve;

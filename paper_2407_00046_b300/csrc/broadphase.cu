@@ -21,10 +21,36 @@ namespace {
 constexpr int kOff = 1 << 20;
 constexpr int64_t kMaxCellsPerPrim = 1 << 20;
 
+// Per-vertex inflation radius r_v; a primitive's radius is the max over its
+// nodes. Pairs (P, Q) are kept when their boxes inflated by r_P and r_Q overlap.
+//   uniform (mode 0): r_v = r/2, every pair, so boxes within r are kept;
+//   motion (mode 1 / 2): r_v = (|p_v - pbar_B| [+ |pbar_B|]) / eta + dhat/2 with
+//     pbar_B the mean displacement of v's body; mode 1 keeps same-body pairs
+//     only (no |pbar_B| term), mode 2 different-body pairs only.
 struct Grid {
   double inv_c;
-  double r;
+  double half_r;     // uniform: r/2
+  double rmax;       // max r_v of this pass (triangles / edges are inserted inflated by r_P + rmax)
+  int mode;
+  const double* dir;
+  const double* bmean;   // [nbody][3]
+  const int32_t* body;   // [nv]
+  double eta, base;
 };
+
+__device__ inline double vert_r(const Grid& G, int v) {
+  if (G.mode == 0) return G.half_r;
+  const int b = G.body[v];
+  const d3 pb = d3{G.bmean[3 * b], G.bmean[3 * b + 1], G.bmean[3 * b + 2]};
+  const d3 w = ld3(G.dir, v) - pb;
+  double r = sqrt(dot(w, w));
+  if (G.mode == 2) r += sqrt(dot(pb, pb));
+  return r / G.eta + G.base;
+}
+__device__ inline bool body_ok(const Grid& G, int va, int vb) {
+  if (G.mode == 0) return true;
+  return G.mode == 1 ? G.body[va] == G.body[vb] : G.body[va] != G.body[vb];
+}
 
 __device__ inline int cell_of(double v, double inv_c) {
   double f = floor(v * inv_c);
@@ -70,13 +96,19 @@ __device__ inline void prim_verts(const Dev& S, int kind, int id, int v[3], int&
   }
 }
 
+__device__ inline double prim_r(const Grid& G, const int* v, int nv) {
+  double r = vert_r(G, v[0]);
+  for (int k = 1; k < nv; ++k) r = fmax(r, vert_r(G, v[k]));
+  return r;
+}
+
 // number of cells of each inflated primitive box (kind 0 = triangles, 1 = edges)
 __global__ void k_count_cells(Dev S, const double* __restrict__ x, int kind, int n, Grid G,
                               int64_t* __restrict__ count) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int v[3], nv;
     prim_verts(S, kind, i, v, nv);
-    const Box b = inflate(prim_box(x, v, nv), G.r);
+    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv) + G.rmax);
     const int64_t c = (int64_t)(cell_of(b.hi.x, G.inv_c) - cell_of(b.lo.x, G.inv_c) + 1) *
                       (cell_of(b.hi.y, G.inv_c) - cell_of(b.lo.y, G.inv_c) + 1) *
                       (cell_of(b.hi.z, G.inv_c) - cell_of(b.lo.z, G.inv_c) + 1);
@@ -90,7 +122,7 @@ __global__ void k_fill_cells(Dev S, const double* __restrict__ x, int kind, int 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int v[3], nv;
     prim_verts(S, kind, i, v, nv);
-    const Box b = inflate(prim_box(x, v, nv), G.r);
+    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv) + G.rmax);
     const int x0 = cell_of(b.lo.x, G.inv_c), x1 = cell_of(b.hi.x, G.inv_c);
     const int y0 = cell_of(b.lo.y, G.inv_c), y1 = cell_of(b.hi.y, G.inv_c);
     const int z0 = cell_of(b.lo.z, G.inv_c), z1 = cell_of(b.hi.z, G.inv_c);
@@ -133,7 +165,8 @@ __global__ void k_pt_query(Dev S, const double* __restrict__ x, Grid G,
       int tv[3], nv;
       prim_verts(S, 0, t, tv, nv);
       if (tv[0] == v || tv[1] == v || tv[2] == v) continue;
-      const Box b = inflate(prim_box(x, tv, 3), G.r);
+      if (!body_ok(G, v, tv[0])) continue;
+      const Box b = inflate(prim_box(x, tv, 3), prim_r(G, tv, 3) + vert_r(G, v));
       if (p.x < b.lo.x || p.x > b.hi.x || p.y < b.lo.y || p.y > b.hi.y || p.z < b.lo.z ||
           p.z > b.hi.z)
         continue;
@@ -149,6 +182,7 @@ __global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
     int ev[3], nv;
     prim_verts(S, 1, e, ev, nv);
     const Box be = prim_box(x, ev, 2);
+    const double re = prim_r(G, ev, 2);
     const int x0 = cell_of(be.lo.x, G.inv_c), x1 = cell_of(be.hi.x, G.inv_c);
     const int y0 = cell_of(be.lo.y, G.inv_c), y1 = cell_of(be.hi.y, G.inv_c);
     const int z0 = cell_of(be.lo.z, G.inv_c), z1 = cell_of(be.hi.z, G.inv_c);
@@ -162,8 +196,12 @@ __global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
             int fv[3];
             prim_verts(S, 1, f, fv, nv);
             if (fv[0] == ev[0] || fv[0] == ev[1] || fv[1] == ev[0] || fv[1] == ev[1]) continue;
-            const Box bf = inflate(prim_box(x, fv, 2), G.r);
-            if (!overlap(be, bf)) continue;
+            if (!body_ok(G, ev[0], fv[0])) continue;
+            const Box bf0 = prim_box(x, fv, 2);
+            const double rf = prim_r(G, fv, 2);
+            if (!overlap(inflate(be, re), inflate(bf0, rf))) continue;
+            // canonical cell: lower corner of box(e) n (box(f) inflated as inserted)
+            const Box bf = inflate(bf0, rf + G.rmax);
             const d3 lo = d3{fmax(be.lo.x, bf.lo.x), fmax(be.lo.y, bf.lo.y), fmax(be.lo.z, bf.lo.z)};
             if (cell_of(lo.x, G.inv_c) != ix || cell_of(lo.y, G.inv_c) != iy ||
                 cell_of(lo.z, G.inv_c) != iz)
@@ -216,39 +254,61 @@ bal_status build_cells(Scene& S, const double* x, int kind, int n, Grid G, int64
   return BAL_OK;
 }
 
-}  // namespace
+__global__ void k_body_mean(Dev S, const int32_t* __restrict__ body, const double* __restrict__ dir,
+                            double* __restrict__ bsum) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x)
+    atomic_add3(bsum, body[v], ld3(dir, v));
+}
+__global__ void k_body_div(double* bsum, const double* __restrict__ inv_cnt, int nb) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    bsum[3 * b] *= inv_cnt[b];
+    bsum[3 * b + 1] *= inv_cnt[b];
+    bsum[3 * b + 2] *= inv_cnt[b];
+  }
+}
+template <int NT>
+__global__ void __launch_bounds__(NT) k_rmax(Dev S, Grid G, double* partials) {
+  double m = 0.0;
+  for (int v = blockIdx.x * NT + threadIdx.x; v < S.nv; v += gridDim.x * NT) m = fmax(m, vert_r(G, v));
+  m = block_max<double, NT>(m, 0.0);
+  if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
 
-bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt, int64_t* n,
-                           cudaStream_t st) {
-  Grid G;
-  const double c = 2.0 * r + 1.5 * S.mean_edge;
-  G.inv_c = 1.0 / c;
-  G.r = r;
+// one grid pass appending to out (counter not reset here)
+bal_status grid_pass(Scene& S, const double* x, Grid& G, Buf& out, int64_t cap,
+                     unsigned long long* counter, cudaStream_t st) {
+  G.inv_c = 1.0 / (4.0 * G.rmax + 1.5 * S.mean_edge);
+  int64_t ncell = 0;
+  uint64_t* cells = nullptr;
+  int32_t* ids = nullptr;
+  BAL_TRY(build_cells(S, x, 0, S.d.nf, G, &ncell, &cells, &ids, st));
+  if (ncell > 0 && S.d.nsv > 0) {
+    k_pt_query<<<grid_for(S.d.nsv), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
+                                                        out.as<uint64_t>(), counter, cap);
+    BAL_LAUNCH_CHECK();
+  }
+  BAL_TRY(build_cells(S, x, 1, S.d.ne, G, &ncell, &cells, &ids, st));
+  if (ncell > 0) {
+    k_ee_query<<<grid_for(S.d.ne), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
+                                                       out.as<uint64_t>(), counter, cap);
+    BAL_LAUNCH_CHECK();
+  }
+  return BAL_OK;
+}
+
+// runs the passes, growing `out` until the pairs fit, then sorts the keys
+bal_status collect(Scene& S, const double* x, Grid* passes, int npass, Buf& out, Buf& alt,
+                   int64_t* n, cudaStream_t st) {
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(S.scal + 63);
   int64_t cap = (int64_t)(out.cap / sizeof(uint64_t));
   if (cap < 1024) {
     BAL_TRY(buf_reserve(out, sizeof(uint64_t) * 1024));
-    cap = 1024;
+    cap = (int64_t)(out.cap / sizeof(uint64_t));
   }
   unsigned long long found = 0;
   for (int attempt = 0; attempt < 2; ++attempt) {
     BAL_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
-    // PT: triangles in cells, vertices query
-    int64_t ncell = 0;
-    uint64_t* cells = nullptr;
-    int32_t* ids = nullptr;
-    BAL_TRY(build_cells(S, x, 0, S.d.nf, G, &ncell, &cells, &ids, st));
-    if (ncell > 0 && S.d.nsv > 0) {
-      k_pt_query<<<grid_for(S.d.nsv), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
-                                                          out.as<uint64_t>(), counter, cap);
-      BAL_LAUNCH_CHECK();
-    }
-    BAL_TRY(build_cells(S, x, 1, S.d.ne, G, &ncell, &cells, &ids, st));
-    if (ncell > 0) {
-      k_ee_query<<<grid_for(S.d.ne), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
-                                                         out.as<uint64_t>(), counter, cap);
-      BAL_LAUNCH_CHECK();
-    }
+    for (int k = 0; k < npass; ++k) BAL_TRY(grid_pass(S, x, passes[k], out, cap, counter, st));
     BAL_CUDA(cudaMemcpyAsync(&found, counter, sizeof(found), cudaMemcpyDeviceToHost, st));
     BAL_CUDA(cudaStreamSynchronize(st));
     if ((int64_t)found <= cap) break;
@@ -257,8 +317,8 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
                 (long long)S.pair_limit);
       return BAL_ERR_CAPACITY;
     }
-    cap = (int64_t)(found + found / 4 + 1024);
-    BAL_TRY(buf_reserve(out, sizeof(uint64_t) * cap));
+    BAL_TRY(buf_reserve(out, sizeof(uint64_t) * (found + found / 4 + 1024)));
+    cap = (int64_t)(out.cap / sizeof(uint64_t));
   }
   *n = (int64_t)found;
   if (found > 1) {
@@ -271,6 +331,48 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
     if (dk.Current() != out.as<uint64_t>()) std::swap(out, alt);
   }
   return BAL_OK;
+}
+
+}  // namespace
+
+bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt, int64_t* n,
+                           cudaStream_t st) {
+  Grid G{};
+  G.mode = 0;
+  G.half_r = 0.5 * r;
+  G.rmax = 0.5 * r;
+  return collect(S, x, &G, 1, out, alt, n, st);
+}
+
+bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, Buf& out, Buf& alt,
+                                  int64_t* n, cudaStream_t st) {
+  // per-body mean displacement of the step
+  BAL_CUDA(cudaMemsetAsync(S.bmean, 0, sizeof(double) * 3 * S.nbody, st));
+  k_body_mean<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.body, dir, S.bmean);
+  BAL_LAUNCH_CHECK();
+  k_body_div<<<grid_for(S.nbody), kThreads, 0, st>>>(S.bmean, S.body_inv_cnt, S.nbody);
+  BAL_LAUNCH_CHECK();
+  Grid P[2];
+  for (int k = 0; k < 2; ++k) {
+    P[k] = Grid{};
+    P[k].mode = 1 + k;
+    P[k].dir = dir;
+    P[k].bmean = S.bmean;
+    P[k].body = S.body;
+    P[k].eta = S.prm.step_bound;
+    P[k].base = 0.5 * S.d.dhat;
+    constexpr int NT = 256;
+    k_rmax<NT><<<2 * kNumSM, NT, 0, st>>>(S.d, P[k], S.partials);
+    BAL_LAUNCH_CHECK();
+    BAL_TRY(finish_reduce(S, 2 * kNumSM, 15 + k, RED_MAX, st));
+  }
+  double rm[2];
+  BAL_CUDA(cudaMemcpyAsync(rm, S.scal + 15, sizeof(rm), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  P[0].rmax = rm[0];
+  P[1].rmax = rm[1];
+  const int npass = S.nbody > 1 ? 2 : 1;
+  return collect(S, x, P, npass, out, alt, n, st);
 }
 
 }  // namespace bal

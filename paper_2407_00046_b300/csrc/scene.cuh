@@ -95,6 +95,11 @@ struct Scene {
   double *xt = nullptr, *grad = nullptr, *gtmp = nullptr, *xtrial = nullptr, *dir = nullptr;
   double *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_x = nullptr;
   double* pnorm = nullptr;       // [nv] |p_v|
+  // bodies (connected components of the tet mesh)
+  int32_t nbody = 0;
+  int32_t* body = nullptr;        // [nv]
+  double* body_inv_cnt = nullptr; // [nbody]
+  double* bmean = nullptr;        // [nbody][3]
   // reductions
   double* partials = nullptr;    // [kMaxPartials]
   double* scal = nullptr;        // [64] scalar results
@@ -145,6 +150,12 @@ bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t
 // out (grown as needed). Returns the count in *n.
 bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt,
                            int64_t* n, cudaStream_t st);
+// Every pair that can satisfy step_bound*d < Delta or d < dhat + Delta along
+// x + alpha dir (alpha <= 1), Delta = max |p_a - p_b|: displacements are split
+// into a per-body mean and a deviation; same-body pairs are inflated by the
+// deviations only, different-body pairs also by |mean|.
+bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, Buf& out,
+                                  Buf& alt, int64_t* n, cudaStream_t st);
 
 // ---- matrix.cu -----------------------------------------------------------------
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
