@@ -203,6 +203,7 @@ bal_status assemble(Scene& S, const double* x, double* g, cudaStream_t st) {
   BAL_TRY(contact_blocks_reduce(S, 6 * S.n_eval, st));
   BAL_TRY(launch_dinv(S, st));
   S.assembled = true;
+  S.f32_valid = false;
   return BAL_OK;
 }
 
@@ -659,6 +660,15 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dalloc(S, &S.pcg_q, 3 * (size_t)nv));
   TRYC(dalloc(S, &S.pcg_x, 3 * (size_t)nv));
   TRYC(dalloc(S, &S.pnorm, (size_t)nv));
+  TRYC(dalloc(S, &S.D32, 9 * (size_t)nv));
+  TRYC(dalloc(S, &S.Dinv32, 9 * (size_t)nv));
+  TRYC(dalloc(S, &S.Lval32, 9 * (size_t)S.d.nnzL));
+  TRYC(dalloc(S, &S.b32, 3 * (size_t)nv));
+  TRYC(dalloc(S, &S.x32, 3 * (size_t)nv));
+  TRYC(dalloc(S, &S.r32, 3 * (size_t)nv));
+  TRYC(dalloc(S, &S.z32, 3 * (size_t)nv));
+  TRYC(dalloc(S, &S.p32, 3 * (size_t)nv));
+  TRYC(dalloc(S, &S.q32, 3 * (size_t)nv));
   TRYC(dalloc(S, &S.partials, (size_t)kMaxPartials));
   TRYC(dalloc(S, &S.scal, 64));
   TRYC(dalloc(S, &S.pcg, 1));
@@ -687,7 +697,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
   if (!sc) return BAL_OK;
   Scene& S = sc->S;
   for (void* p : S.owned) cudaFree(p);
-  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.emit_keys, &S.emit_keys_alt, &S.emit_idx,
+  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_keys_alt, &S.emit_idx,
                  &S.emit_idx_alt, &S.emit_vals, &S.seg_head, &S.seg_pos, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,

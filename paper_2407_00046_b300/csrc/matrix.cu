@@ -99,27 +99,68 @@ __global__ void k_dinv(Dev S) {
   }
 }
 
-__device__ inline d3 mv(const double* __restrict__ B, d3 v) {
-  return d3{B[0] * v.x + B[1] * v.y + B[2] * v.z, B[3] * v.x + B[4] * v.y + B[5] * v.z,
-            B[6] * v.x + B[7] * v.y + B[8] * v.z};
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ inline V3<T> ldv(const T* __restrict__ p, int64_t i) {
+  return V3<T>{p[3 * i], p[3 * i + 1], p[3 * i + 2]};
 }
-__device__ inline d3 mtv(const double* __restrict__ B, d3 v) {
-  return d3{B[0] * v.x + B[3] * v.y + B[6] * v.z, B[1] * v.x + B[4] * v.y + B[7] * v.z,
-            B[2] * v.x + B[5] * v.y + B[8] * v.z};
+template <typename T>
+__device__ inline void stv(T* __restrict__ p, int64_t i, V3<T> v) {
+  p[3 * i] = v.x;
+  p[3 * i + 1] = v.y;
+  p[3 * i + 2] = v.z;
+}
+template <typename T>
+__device__ inline V3<T> addv(V3<T> a, V3<T> b) { return V3<T>{a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ inline V3<T> axpyv(T s, V3<T> a, V3<T> b) {   // b + s a
+  return V3<T>{b.x + s * a.x, b.y + s * a.y, b.z + s * a.z};
+}
+template <typename T>
+__device__ inline T dotv(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ inline V3<T> mv(const T* __restrict__ B, V3<T> v) {
+  return V3<T>{B[0] * v.x + B[1] * v.y + B[2] * v.z, B[3] * v.x + B[4] * v.y + B[5] * v.z,
+               B[6] * v.x + B[7] * v.y + B[8] * v.z};
+}
+template <typename T>
+__device__ inline V3<T> mtv(const T* __restrict__ B, V3<T> v) {
+  return V3<T>{B[0] * v.x + B[3] * v.y + B[6] * v.z, B[1] * v.x + B[4] * v.y + B[7] * v.z,
+               B[2] * v.x + B[5] * v.y + B[8] * v.z};
+}
+template <typename T>
+__device__ inline void atomic_addv(T* p, int64_t i, V3<T> v) {
+  atomicAdd(p + 3 * i, v.x);
+  atomicAdd(p + 3 * i + 1, v.y);
+  atomicAdd(p + 3 * i + 2, v.z);
 }
 
+template <typename T>
 struct OffDiag {
   const int32_t* Lrow;
   const int32_t* Lcol;
-  const double* Lval;
+  const T* Lval;
   int64_t nL;
   const int32_t* Crow;
   const int32_t* Ccol;
-  const double* Cval;
+  const T* Cval;
   int64_t nC;
 };
 
-__device__ inline void block_of(const OffDiag& O, int64_t b, int& i, int& j, const double*& B) {
+// A symmetric block system: diagonal blocks, their inverses, off-diagonal blocks.
+template <typename T>
+struct Sys {
+  const T* D;
+  const T* Dinv;
+  OffDiag<T> O;
+  int nv;
+};
+
+template <typename T>
+__device__ inline void block_of(const OffDiag<T>& O, int64_t b, int& i, int& j, const T*& B) {
   if (b < O.nL) {
     i = O.Lrow[b];
     j = O.Lcol[b];
@@ -132,20 +173,22 @@ __device__ inline void block_of(const OffDiag& O, int64_t b, int& i, int& j, con
   }
 }
 
-__global__ void k_spmv_diag(Dev S, const double* __restrict__ v, double* __restrict__ y) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nv; i += gridDim.x * blockDim.x)
-    st3(y, i, mv(S.D + 9 * (int64_t)i, ld3(v, i)));
+template <typename T>
+__global__ void k_spmv_diag(Sys<T> A, const T* __restrict__ v, T* __restrict__ y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nv; i += gridDim.x * blockDim.x)
+    stv(y, i, mv(A.D + 9 * (int64_t)i, ldv(v, i)));
 }
 
-__global__ void k_spmv_offdiag(OffDiag O, const double* __restrict__ v, double* __restrict__ y) {
+template <typename T>
+__global__ void k_spmv_offdiag(OffDiag<T> O, const T* __restrict__ v, T* __restrict__ y) {
   const int64_t n = O.nL + O.nC;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n;
        b += (int64_t)gridDim.x * blockDim.x) {
     int i, j;
-    const double* B;
+    const T* B;
     block_of(O, b, i, j, B);
-    atomic_add3(y, i, mv(B, ld3(v, j)));
-    atomic_add3(y, j, mtv(B, ld3(v, i)));
+    atomic_addv(y, i, mv(B, ldv(v, j)));
+    atomic_addv(y, j, mtv(B, ldv(v, i)));
   }
 }
 
@@ -166,22 +209,23 @@ __device__ inline double sum_partials(const double* partials, int n) {
   return block_sum<double, NT>(acc);
 }
 
-// r = b - H x (given y = H x), z = D^{-1} r; scalars rz, ||r||, ||b||
-template <int NT>
-__global__ void __launch_bounds__(NT) k_pcg_init(Dev S, const double* __restrict__ b,
-                                                 const double* __restrict__ y, double* __restrict__ r,
-                                                 double* __restrict__ z, PcgScalars* P,
+// r = b - y (y = H x0, or y = null for x0 = 0), z = D^{-1} r; scalars rz, ||r||, ||b||.
+// Dot products accumulate in FP64 whatever T is.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_init(Sys<T> A, const T* __restrict__ b,
+                                                 const T* __restrict__ y, T* __restrict__ r,
+                                                 T* __restrict__ z, PcgScalars* P,
                                                  double* partials, double tol) {
   double rz = 0.0, rr = 0.0, bb = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < S.nv; i += gridDim.x * NT) {
-    const d3 bi = ld3(b, i);
-    const d3 ri = bi - ld3(y, i);
-    const d3 zi = mv(S.Dinv + 9 * (int64_t)i, ri);
-    st3(r, i, ri);
-    st3(z, i, zi);
-    rz += dot(ri, zi);
-    rr += dot(ri, ri);
-    bb += dot(bi, bi);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
+    const V3<T> bi = ldv(b, i);
+    const V3<T> ri = y ? axpyv(T(-1), ldv(y, i), bi) : bi;
+    const V3<T> zi = mv(A.Dinv + 9 * (int64_t)i, ri);
+    stv(r, i, ri);
+    stv(z, i, zi);
+    rz += (double)dotv(ri, zi);
+    rr += (double)dotv(ri, ri);
+    bb += (double)dotv(bi, bi);
   }
   rz = block_sum<double, NT>(rz);
   rr = block_sum<double, NT>(rr);
@@ -214,40 +258,41 @@ __global__ void __launch_bounds__(NT) k_pcg_init(Dev S, const double* __restrict
   }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_pcg_dir_diag(Dev S, const double* __restrict__ z,
-                                                     double* __restrict__ p, double* __restrict__ q,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_dir_diag(Sys<T> A, const T* __restrict__ z,
+                                                     T* __restrict__ p, T* __restrict__ q,
                                                      PcgScalars* P, double* partials) {
   if (P->done) return;
-  const double beta = P->it == 0 ? 0.0 : P->beta;
+  const bool first = P->it == 0;
+  const T beta = (T)P->beta;
   double pdp = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < S.nv; i += gridDim.x * NT) {
-    const d3 pi = P->it == 0 ? ld3(z, i) : ld3(z, i) + beta * ld3(p, i);
-    const d3 qi = mv(S.D + 9 * (int64_t)i, pi);
-    st3(p, i, pi);
-    st3(q, i, qi);
-    pdp += dot(pi, qi);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
+    const V3<T> pi = first ? ldv(z, i) : axpyv(beta, ldv(p, i), ldv(z, i));
+    const V3<T> qi = mv(A.D + 9 * (int64_t)i, pi);
+    stv(p, i, pi);
+    stv(q, i, qi);
+    pdp += (double)dotv(pi, qi);
   }
   pdp = block_sum<double, NT>(pdp);
   if (threadIdx.x == 0) partials[blockIdx.x] = pdp;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag O, const double* __restrict__ p,
-                                                    double* __restrict__ q, PcgScalars* P,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag<T> O, const T* __restrict__ p,
+                                                    T* __restrict__ q, PcgScalars* P,
                                                     double* partials, int n_prev) {
   if (P->done) return;
   const int64_t n = O.nL + O.nC;
   double plp = 0.0;
   for (int64_t b = blockIdx.x * (int64_t)NT + threadIdx.x; b < n; b += (int64_t)gridDim.x * NT) {
     int i, j;
-    const double* B;
+    const T* B;
     block_of(O, b, i, j, B);
-    const d3 pj = ld3(p, j), pi = ld3(p, i);
-    const d3 bpj = mv(B, pj);
-    atomic_add3(q, i, bpj);
-    atomic_add3(q, j, mtv(B, pi));
-    plp += 2.0 * dot(pi, bpj);
+    const V3<T> pj = ldv(p, j), pi = ldv(p, i);
+    const V3<T> bpj = mv(B, pj);
+    atomic_addv(q, i, bpj);
+    atomic_addv(q, j, mtv(B, pi));
+    plp += 2.0 * (double)dotv(pi, bpj);
   }
   plp = block_sum<double, NT>(plp);
   if (threadIdx.x == 0) partials[n_prev + blockIdx.x] = plp;
@@ -265,23 +310,22 @@ __global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag O, const double* __r
   }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_pcg_update(Dev S, double* __restrict__ x,
-                                                   const double* __restrict__ p,
-                                                   const double* __restrict__ q, double* __restrict__ r,
-                                                   double* __restrict__ z, PcgScalars* P,
-                                                   double* partials) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_update(Sys<T> A, T* __restrict__ x,
+                                                   const T* __restrict__ p, const T* __restrict__ q,
+                                                   T* __restrict__ r, T* __restrict__ z,
+                                                   PcgScalars* P, double* partials) {
   if (P->done) return;
-  const double alpha = P->alpha;
+  const T alpha = (T)P->alpha;
   double rz = 0.0, rr = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < S.nv; i += gridDim.x * NT) {
-    st3(x, i, ld3(x, i) + alpha * ld3(p, i));
-    const d3 ri = ld3(r, i) - alpha * ld3(q, i);
-    const d3 zi = mv(S.Dinv + 9 * (int64_t)i, ri);
-    st3(r, i, ri);
-    st3(z, i, zi);
-    rz += dot(ri, zi);
-    rr += dot(ri, ri);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
+    stv(x, i, axpyv(alpha, ldv(p, i), ldv(x, i)));
+    const V3<T> ri = axpyv(-alpha, ldv(q, i), ldv(r, i));
+    const V3<T> zi = mv(A.Dinv + 9 * (int64_t)i, ri);
+    stv(r, i, ri);
+    stv(z, i, zi);
+    rz += (double)dotv(ri, zi);
+    rr += (double)dotv(ri, ri);
   }
   rz = block_sum<double, NT>(rz);
   rr = block_sum<double, NT>(rr);
@@ -319,17 +363,95 @@ __global__ void __launch_bounds__(NT) k_pcg_update(Dev S, double* __restrict__ x
   }
 }
 
-OffDiag offdiag_of(Scene& S) {
-  OffDiag O;
-  O.Lrow = S.d.L_row;
-  O.Lcol = S.d.L_col;
-  O.Lval = S.d.Lval;
-  O.nL = S.d.nnzL;
-  O.Crow = S.C_row.as<int32_t>();
-  O.Ccol = S.C_col.as<int32_t>();
-  O.Cval = S.C_val.as<double>();
-  O.nC = S.nnzC;
-  return O;
+template <typename T>
+__global__ void k_convert(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+// x += s * (double)e ; also r = 0 for the next residual pass
+__global__ void k_refine_update(int64_t n, double s, const float* __restrict__ e, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += s * (double)e[i];
+}
+// r32 = (float)(r * s)
+__global__ void k_scale_to_f32(int64_t n, double s, const double* __restrict__ r, float* __restrict__ o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (float)(s * r[i]);
+}
+__global__ void k_sub(int64_t n, const double* __restrict__ b, const double* __restrict__ y,
+                      double* __restrict__ r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+
+Sys<double> sys64(Scene& S) {
+  Sys<double> A;
+  A.D = S.d.D;
+  A.Dinv = S.d.Dinv;
+  A.O = OffDiag<double>{S.d.L_row, S.d.L_col, S.d.Lval, S.d.nnzL, S.C_row.as<int32_t>(),
+                        S.C_col.as<int32_t>(), S.C_val.as<double>(), S.nnzC};
+  A.nv = S.d.nv;
+  return A;
+}
+Sys<float> sys32(Scene& S) {
+  Sys<float> A;
+  A.D = S.D32;
+  A.Dinv = S.Dinv32;
+  A.O = OffDiag<float>{S.d.L_row, S.d.L_col, S.Lval32, S.d.nnzL, S.C_row.as<int32_t>(),
+                       S.C_col.as<int32_t>(), S.C_val32.as<float>(), S.nnzC};
+  A.nv = S.d.nv;
+  return A;
+}
+
+template <typename T>
+bal_status spmv_t(const Sys<T>& A, const T* v, T* y, cudaStream_t st) {
+  k_spmv_diag<T><<<grid_for(A.nv), kThreads, 0, st>>>(A, v, y);
+  BAL_LAUNCH_CHECK();
+  if (A.O.nL + A.O.nC > 0) {
+    k_spmv_offdiag<T><<<grid_for(A.O.nL + A.O.nC, kThreads, kNumSM * 16), kThreads, 0, st>>>(A.O, v, y);
+    BAL_LAUNCH_CHECK();
+  }
+  return BAL_OK;
+}
+
+// Block-Jacobi PCG on system A from x (x0 = 0 if y0 is null, else y0 = A x0).
+template <typename T>
+bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T* r, T* z, T* p,
+                    T* q, double tol, int max_it, int window, PcgScalars* hout, cudaStream_t st) {
+  constexpr int NT = kRedThreads;
+  const int G = kRedBlocks;
+  PcgScalars init{};
+  init.max_it = max_it;
+  init.window = window > 0 ? window : (1 << 30);
+  BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_pcg_init<T, NT><<<G, NT, 0, st>>>(A, b, y0, r, z, S.pcg, S.partials, tol);
+  BAL_LAUNCH_CHECK();
+  PcgScalars h{};
+  const int chunk = 16;
+  int launched = 0;
+  for (;;) {
+    BAL_CUDA(cudaMemcpyAsync(&h, S.pcg, sizeof(h), cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+    if (h.done || launched >= max_it) break;
+    const int n = std::min(chunk, max_it - launched);
+    for (int k = 0; k < n; ++k) {
+      k_pcg_dir_diag<T, NT><<<G, NT, 0, st>>>(A, z, p, q, S.pcg, S.partials);
+      k_pcg_offdiag<T, NT><<<G, NT, 0, st>>>(A.O, p, q, S.pcg, S.partials, G);
+      k_pcg_update<T, NT><<<G, NT, 0, st>>>(A, x, p, q, r, z, S.pcg, S.partials);
+    }
+    BAL_LAUNCH_CHECK();
+    launched += n;
+  }
+  *hout = h;
+  if (h.done == 2 || h.done == 3) {
+    set_error("pcg: %s at iteration %d", h.done == 2 ? "non-finite residual" : "p^T H p <= 0", h.it);
+    return BAL_ERR_NAN;
+  }
+  return BAL_OK;
 }
 
 }  // namespace
@@ -385,49 +507,116 @@ bal_status launch_dinv(Scene& S, cudaStream_t st) {
   return BAL_OK;
 }
 
-bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st) {
-  k_spmv_diag<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, v, y);
+bal_status make_f32_copy(Scene& S, cudaStream_t st) {
+  const int64_t n9 = 9 * (int64_t)S.d.nv;
+  k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.D, S.D32);
+  k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.Dinv, S.Dinv32);
+  if (S.d.nnzL)
+    k_convert<float><<<grid_for(9 * S.d.nnzL), kThreads, 0, st>>>(9 * S.d.nnzL, S.d.Lval, S.Lval32);
+  BAL_TRY(buf_reserve(S.C_val32, sizeof(float) * 9 * (S.nnzC + 1)));
+  if (S.nnzC)
+    k_convert<float><<<grid_for(9 * S.nnzC), kThreads, 0, st>>>(9 * S.nnzC, S.C_val.as<double>(),
+                                                                 S.C_val32.as<float>());
   BAL_LAUNCH_CHECK();
-  const OffDiag O = offdiag_of(S);
-  if (O.nL + O.nC > 0) {
-    k_spmv_offdiag<<<grid_for(O.nL + O.nC, kThreads, kNumSM * 16), kThreads, 0, st>>>(O, v, y);
+  return BAL_OK;
+}
+
+bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st) {
+  return spmv_t(sys64(S), v, y, st);
+}
+
+bal_status spmv32(Scene& S, const float* v, float* y, cudaStream_t st) {
+  return spmv_t(sys32(S), v, y, st);
+}
+
+static bal_status true_residual(Scene& S, const double* b, const double* x, double* rn, double* bn,
+                                cudaStream_t st) {
+  BAL_TRY(spmv(S, x, S.pcg_q, st));
+  BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
+  double res[2];
+  BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  *rn = sqrt(res[0]);
+  *bn = sqrt(res[1]);
+  return BAL_OK;
+}
+
+// FP32 inner PCG on the FP32 copy of H, FP64 outer residual and correction
+// (iterative refinement): r = b - H x (FP64), solve H e = r/||r|| in FP32 to
+// mixed_inner_tol, x += ||r|| e, repeat until ||r|| <= tol ||r_0||.
+static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, int max_it,
+                            bal_solve_info* info, cudaStream_t st) {
+  if (!S.f32_valid) {
+    BAL_TRY(make_f32_copy(S, st));
+    S.f32_valid = true;
+  }
+  const int64_t n3 = 3 * (int64_t)S.d.nv;
+  BAL_TRY(spmv(S, x, S.pcg_q, st));
+  k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
+  BAL_LAUNCH_CHECK();
+  double rn, bn;
+  BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
+  {
+    double res[2];
+    BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+    rn = sqrt(res[0]);
+    bn = sqrt(res[1]);
+  }
+  const double r0 = rn;
+  int total = 0, passes = 0;
+  bool converged = rn <= tol * r0 || rn == 0.0;
+  const Sys<float> A = sys32(S);
+  while (!converged && passes < S.prm.mixed_max_refine && total < max_it) {
+    k_scale_to_f32<<<grid_for(n3), kThreads, 0, st>>>(n3, 1.0 / rn, S.pcg_r, S.b32);
+    BAL_CUDA(cudaMemsetAsync(S.x32, 0, sizeof(float) * n3, st));
     BAL_LAUNCH_CHECK();
+    PcgScalars h;
+    const int inner = std::min(S.prm.mixed_inner_max, max_it - total);
+    const double itol = std::max(S.prm.mixed_inner_tol, 0.5 * tol * r0 / rn);
+    BAL_TRY(pcg_core<float>(S, A, S.b32, nullptr, S.x32, S.r32, S.z32, S.p32, S.q32, itol, inner,
+                            S.prm.pcg_stall_window, &h, st));
+    total += h.it;
+    passes += 1;
+    k_refine_update<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, S.x32, x);
+    BAL_LAUNCH_CHECK();
+    BAL_TRY(spmv(S, x, S.pcg_q, st));
+    k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
+    BAL_LAUNCH_CHECK();
+    BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
+    double res[2];
+    BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+    const double rn_new = sqrt(res[0]);
+    if (!std::isfinite(rn_new)) {
+      set_error("mixed pcg: non-finite residual after refinement pass %d", passes);
+      return BAL_ERR_NAN;
+    }
+    const bool progress = rn_new < 0.99 * rn;
+    rn = rn_new;
+    converged = rn <= tol * r0;
+    if (!progress || h.it == 0) break;
+  }
+  if (info) {
+    info->iters = total;
+    info->rel_residual = bn > 0 ? rn / bn : rn;
+    info->rel_residual_r0 = r0 > 0 ? rn / r0 : rn;
+    info->stagnated = converged ? 0 : 1;
+    info->converged = converged ? 1 : 0;
+    info->refine_passes = passes;
+    info->warm_iters = 0;
+    info->n_groups = 0;
   }
   return BAL_OK;
 }
 
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
                      bal_solve_info* info, cudaStream_t st) {
-  constexpr int NT = kRedThreads;
-  const int G = kRedBlocks;
-  double* r = S.pcg_r;
-  double* z = S.pcg_z;
-  double* p = S.pcg_p;
-  double* q = S.pcg_q;
-  PcgScalars init{};
-  init.max_it = max_it;
-  init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
-  BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-  BAL_TRY(spmv(S, x, q, st));
-  k_pcg_init<NT><<<G, NT, 0, st>>>(S.d, b, q, r, z, S.pcg, S.partials, tol);
-  BAL_LAUNCH_CHECK();
-  const OffDiag O = offdiag_of(S);
-  PcgScalars h{};
-  const int chunk = 16;
-  int launched = 0;
-  for (;;) {
-    BAL_CUDA(cudaMemcpyAsync(&h, S.pcg, sizeof(h), cudaMemcpyDeviceToHost, st));
-    BAL_CUDA(cudaStreamSynchronize(st));
-    if (h.done || launched >= max_it) break;
-    const int n = std::min(chunk, max_it - launched);
-    for (int k = 0; k < n; ++k) {
-      k_pcg_dir_diag<NT><<<G, NT, 0, st>>>(S.d, z, p, q, S.pcg, S.partials);
-      k_pcg_offdiag<NT><<<G, NT, 0, st>>>(O, p, q, S.pcg, S.partials, G);
-      k_pcg_update<NT><<<G, NT, 0, st>>>(S.d, x, p, q, r, z, S.pcg, S.partials);
-    }
-    BAL_LAUNCH_CHECK();
-    launched += n;
-  }
+  if (S.prm.precision == BAL_PREC_MIXED) return pcg_mixed(S, b, x, tol, max_it, info, st);
+  BAL_TRY(spmv(S, x, S.pcg_q, st));
+  PcgScalars h;
+  BAL_TRY(pcg_core<double>(S, sys64(S), b, S.pcg_q, x, S.pcg_r, S.pcg_z, S.pcg_p, S.pcg_q, tol,
+                           max_it, S.prm.pcg_stall_window, &h, st));
   if (info) {
     info->iters = h.it;
     info->stagnated = h.stagnated;
@@ -435,19 +624,10 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
     info->refine_passes = 0;
     info->warm_iters = 0;
     info->n_groups = 0;
-    // true residual, FP64
-    BAL_TRY(spmv(S, x, q, st));
-    BAL_TRY(launch_residual_norm(S, b, q, st));
-    double res[2];
-    BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
-    BAL_CUDA(cudaStreamSynchronize(st));
-    const double rn = sqrt(res[0]), bn = sqrt(res[1]);
+    double rn, bn;
+    BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
     info->rel_residual = bn > 0 ? rn / bn : rn;
     info->rel_residual_r0 = h.r0norm > 0 ? rn / h.r0norm : rn;
-  }
-  if (h.done == 2 || h.done == 3) {
-    set_error("pcg: %s at iteration %d", h.done == 2 ? "non-finite residual" : "p^T H p <= 0", h.it);
-    return BAL_ERR_NAN;
   }
   return BAL_OK;
 }

@@ -74,7 +74,11 @@ struct Scene {
 
   // contact part of the matrix
   int64_t nnzC = 0;
-  Buf C_row, C_col, C_val;
+  Buf C_row, C_col, C_val, C_val32;
+  // FP32 copies for the mixed-precision solve (valid after make_f32_copy)
+  float *D32 = nullptr, *Dinv32 = nullptr, *Lval32 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  bool f32_valid = false;
   bool assembled = false;
 
   // contact emission + sort scratch
@@ -161,6 +165,8 @@ bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, 
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
 bal_status launch_dinv(Scene& S, cudaStream_t st);
 bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
+bal_status spmv32(Scene& S, const float* v, float* y, cudaStream_t st);
+bal_status make_f32_copy(Scene& S, cudaStream_t st);
 // S.scal[8] = ||b - y||^2, S.scal[9] = ||b||^2
 bal_status launch_residual_norm(Scene& S, const double* b, const double* y, cudaStream_t st);
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,

@@ -165,3 +165,40 @@ def test_newton_step_counts_match_oracle():
     keys, _ = obal.active_pairs(m, sc.X)
     assert info["n_active"] == len(keys) and info["n_active"] > 0
     assert info["alpha"] > 0
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_mixed_precision_pcg_refines_to_fp64_residual(contact_case, tol):
+    # FP32 SpMV / preconditioner inside, FP64 residual outside (iterative refinement)
+    sc, S, x = contact_case
+    S.set_al_state(3.0, 3.0)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    S.assemble_hessian(T(x), g)
+    m, y, ps = oracle_state(sc, x, 3.0)
+    H_or = system.hessian(m, x, y, ps, 3.0)
+    S.set_params(precision=bal.PREC_MIXED, mixed_inner_tol=1e-4, mixed_max_refine=30)
+    try:
+        b = -g
+        sol = torch.zeros_like(b)
+        info = S.pcg_solve(b, sol, tol, 20000)
+    finally:
+        S.set_params(precision=bal.PREC_FP64)
+    bn = b.cpu().numpy()
+    res = np.linalg.norm(bn - H_or @ sol.cpu().numpy()) / np.linalg.norm(bn)
+    assert info["converged"] == 1 and info["refine_passes"] >= 1
+    assert res <= 1.05 * tol, (res, info)
+
+
+def test_mixed_precision_trajectory_matches_oracle():
+    sc = close_cubes(n=2, gap=5e-4)
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12, pcg_max_iter=20000,
+                                         precision=bal.PREC_MIXED, mixed_inner_tol=1e-4,
+                                         mixed_max_refine=40))
+    m = system.make_model(sc)
+    x, v = T(sc.X), T(sc.V0)
+    xo, vo = sc.X.copy(), sc.V0.copy()
+    for _ in range(2):
+        info = S.time_step(x, v)
+        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8))
+        assert info["converged"] == 1
+        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
