@@ -117,8 +117,17 @@ def run_ours(args, rank, world):
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
     v = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
     log = []
-    for _ in range(args.warmup):
+
+    def progress(tag, info):
+        print(f"[bench] {tag}: status {info['status']} newton {info['newton_iters']} pcg "
+              f"{info['pcg_iters_total']} max|A| {info['max_active']} min d {info['min_distance']:.3e} "
+              f"ms {info['ms_total']:.0f} (asm {info['ms_assemble']:.0f} solve {info['ms_solve']:.0f} "
+              f"ls {info['ms_line_search']:.0f} contact {info['ms_contact']:.0f})",
+              file=sys.stderr, flush=True)
+
+    for w in range(args.warmup):
         log.append(S.time_step(x, v, check=False))
+        progress(f"warmup {w}", log[-1])
     x0, v0 = x.clone(), v.clone()
     if world > 1:
         torch.distributed.barrier()
@@ -131,6 +140,8 @@ def run_ours(args, rank, world):
             timed.append(S.time_step(x, v, check=False))
         e1.record(stream)
         torch.cuda.synchronize()
+    for k, t in enumerate(timed):
+        progress(f"timed {k}", t)
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)

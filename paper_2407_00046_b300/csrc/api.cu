@@ -97,25 +97,33 @@ inline double barrier_d2b(double d, double c) {
   return -2.0 * std::log(d / c) - 4.0 * t / d + t * t / (d * d);
 }
 
-// A at x: candidates within dhat, exact distances, keep d < dhat (host copies).
+// A at x: candidates within dhat, exact distances, keep d < dhat (compacted on
+// the device; host copies of A only).
 bal_status detect_active(Scene& S, const double* x, std::vector<uint64_t>& keys,
                          std::vector<double>& dist, cudaStream_t st) {
   BAL_TRY(find_candidates(S, x, S.d.dhat, S.cand, S.cand_alt, &S.n_cand, st));
   keys.clear();
   dist.clear();
   if (S.n_cand == 0) return BAL_OK;
-  BAL_TRY(buf_reserve(S.dist, sizeof(double) * S.n_cand));
-  BAL_TRY(launch_pair_distance(S, x, S.cand.as<uint64_t>(), S.n_cand, S.dist.as<double>(), st));
-  std::vector<uint64_t> ck(S.n_cand);
-  std::vector<double> cd(S.n_cand);
-  BAL_CUDA(cudaMemcpyAsync(ck.data(), S.cand.p, sizeof(uint64_t) * S.n_cand, cudaMemcpyDeviceToHost, st));
-  BAL_CUDA(cudaMemcpyAsync(cd.data(), S.dist.p, sizeof(double) * S.n_cand, cudaMemcpyDeviceToHost, st));
-  BAL_CUDA(cudaStreamSynchronize(st));
-  for (int64_t i = 0; i < S.n_cand; ++i)
-    if (cd[i] < S.d.dhat) {
-      keys.push_back(ck[i]);
-      dist.push_back(cd[i]);
-    }
+  const int64_t n = S.n_cand;
+  BAL_TRY(buf_reserve(S.dist, sizeof(double) * n));
+  BAL_TRY(buf_reserve(S.dist_alt, sizeof(double) * n));
+  BAL_TRY(buf_reserve(S.flags, n));
+  BAL_TRY(buf_reserve(S.cand_alt, sizeof(uint64_t) * n));
+  BAL_TRY(launch_pair_distance(S, x, S.cand.as<uint64_t>(), n, S.dist.as<double>(), st));
+  BAL_TRY(launch_flag_below(S.dist.as<double>(), n, S.d.dhat, S.flags.as<uint8_t>(), st));
+  int64_t na = 0, nd = 0;
+  BAL_TRY(compact_u64(S, S.cand.as<uint64_t>(), S.flags.as<uint8_t>(), n, S.cand_alt.as<uint64_t>(),
+                      &na, st));
+  BAL_TRY(compact_f64(S, S.dist.as<double>(), S.flags.as<uint8_t>(), n, S.dist_alt.as<double>(), &nd,
+                      st));
+  keys.resize(na);
+  dist.resize(na);
+  if (na) {
+    BAL_CUDA(cudaMemcpyAsync(keys.data(), S.cand_alt.p, sizeof(uint64_t) * na, cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaMemcpyAsync(dist.data(), S.dist_alt.p, sizeof(double) * na, cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+  }
   return BAL_OK;
 }
 
@@ -360,6 +368,17 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   bool extra_done = false;
   for (;;) {
     BAL_TRY(find_candidates_motion(S, x, S.dir, S.ls_cand, S.ls_cand_alt, &S.n_ls_cand, st));
+    if (S.n_ls_cand > 0) {   // keep the pairs that can enter A or bound alpha
+      BAL_TRY(buf_reserve(S.flags, S.n_ls_cand));
+      BAL_TRY(buf_reserve(S.ls_cand_alt, sizeof(uint64_t) * S.n_ls_cand));
+      BAL_TRY(launch_ls_filter(S, x, S.dir, S.ls_cand.as<uint64_t>(), S.n_ls_cand,
+                               S.flags.as<uint8_t>(), st));
+      int64_t nk = 0;
+      BAL_TRY(compact_u64(S, S.ls_cand.as<uint64_t>(), S.flags.as<uint8_t>(), S.n_ls_cand,
+                          S.ls_cand_alt.as<uint64_t>(), &nk, st));
+      std::swap(S.ls_cand, S.ls_cand_alt);
+      S.n_ls_cand = nk;
+    }
     I.n_candidates = S.n_ls_cand;
     double alpha = 1.0;
     if (S.n_ls_cand > 0) {
@@ -700,7 +719,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
   Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_keys_alt, &S.emit_idx,
                  &S.emit_idx_alt, &S.emit_vals, &S.seg_head, &S.seg_pos, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
-                 &S.cand_alt, &S.dist, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
+                 &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
                  &S.ls_cand, &S.ls_cand_alt, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d};
   for (Buf* b : bufs) buf_free(*b);
   delete sc;

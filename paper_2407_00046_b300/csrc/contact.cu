@@ -555,6 +555,38 @@ __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restri
   if (threadIdx.x == 0) partials[blockIdx.x] = amin;
 }
 
+// keeps a line-search candidate if it can enter A along the step (d < dhat +
+// Delta) or can constrain the step length (eta d < Delta); Delta = max |p_a - p_b|
+__global__ void k_ls_filter(Dev S, const double* __restrict__ x, const double* __restrict__ dir,
+                            const uint64_t* __restrict__ cand, int64_t nc, double eta,
+                            uint8_t* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const uint64_t key = cand[i];
+    const double d = pair_distance(S, x, key, v, X, R);
+    d3 P[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) P[a] = ld3(dir, v[a]);
+    const int na = key_kind(key) == 0 ? 1 : 2;
+    double Dl = 0.0;
+    for (int a = 0; a < na; ++a)
+      for (int b = na; b < 4; ++b) {
+        const d3 w = P[a] - P[b];
+        Dl = fmax(Dl, sqrt(dot(w, w)));
+      }
+    flag[i] = (d < S.dhat + Dl || eta * d < Dl) ? 1 : 0;
+  }
+}
+
+__global__ void k_flag_below(const double* __restrict__ d, int64_t n, double thr, uint8_t* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = d[i] < thr ? 1 : 0;
+}
+
 __global__ void k_dual_update(Dev S, const double* __restrict__ x, const uint64_t* __restrict__ keys,
                               double* __restrict__ mu, int64_t n, double sigma) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -623,6 +655,21 @@ bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
   k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound, S.partials);
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);
+}
+
+bal_status launch_ls_filter(Scene& S, const double* x, const double* dir, const uint64_t* cand,
+                            int64_t n, uint8_t* flag, cudaStream_t st) {
+  if (n <= 0) return BAL_OK;
+  k_ls_filter<<<grid_for(n), kThreads, 0, st>>>(S.d, x, dir, cand, n, S.prm.step_bound, flag);
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
+}
+
+bal_status launch_flag_below(const double* d, int64_t n, double thr, uint8_t* flag, cudaStream_t st) {
+  if (n <= 0) return BAL_OK;
+  k_flag_below<<<grid_for(n), kThreads, 0, st>>>(d, n, thr, flag);
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
 }
 
 bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t st) {

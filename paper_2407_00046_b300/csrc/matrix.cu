@@ -501,6 +501,35 @@ bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
   return BAL_OK;
 }
 
+template <typename T>
+static bal_status compact_t(Scene& S, const T* in, const uint8_t* flag, int64_t n, T* out,
+                            int64_t* nsel, cudaStream_t st) {
+  int64_t* dn = reinterpret_cast<int64_t*>(S.scal + 62);
+  size_t tmp = 0;
+  BAL_CUDA(cub::DeviceSelect::Flagged(nullptr, tmp, in, flag, out, dn, n, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceSelect::Flagged(S.cub_tmp.p, tmp, in, flag, out, dn, n, st));
+  BAL_CUDA(cudaMemcpyAsync(nsel, dn, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  return BAL_OK;
+}
+bal_status compact_u64(Scene& S, const uint64_t* in, const uint8_t* flag, int64_t n, uint64_t* out,
+                       int64_t* nsel, cudaStream_t st) {
+  if (n <= 0) {
+    *nsel = 0;
+    return BAL_OK;
+  }
+  return compact_t(S, in, flag, n, out, nsel, st);
+}
+bal_status compact_f64(Scene& S, const double* in, const uint8_t* flag, int64_t n, double* out,
+                       int64_t* nsel, cudaStream_t st) {
+  if (n <= 0) {
+    *nsel = 0;
+    return BAL_OK;
+  }
+  return compact_t(S, in, flag, n, out, nsel, st);
+}
+
 bal_status launch_dinv(Scene& S, cudaStream_t st) {
   k_dinv<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d);
   BAL_LAUNCH_CHECK();

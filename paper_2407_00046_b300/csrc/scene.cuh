@@ -89,7 +89,8 @@ struct Scene {
   Buf bp_cells, bp_cells_alt, bp_ids, bp_ids_alt, bp_count, bp_offs;
   Buf cand, cand_alt;            // candidates at r = dhat (sorted keys)
   int64_t n_cand = 0;
-  Buf dist;                      // per-pair distances scratch
+  Buf dist, dist_alt;            // per-pair distances scratch
+  Buf flags;                     // per-pair selection flags
   Buf eval_keys, eval_flags, eval_mu, eval_s;   // evaluation list A u A'
   int64_t n_eval = 0;
   Buf ls_cand, ls_cand_alt;      // line-search candidates
@@ -146,6 +147,10 @@ bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand
 // Delta_i = max |p_a - p_b| over a node of each primitive -> S.scal[slot].
 bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
                              const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st);
+// flag[i] = candidate i can enter A along the step or constrain alpha
+bal_status launch_ls_filter(Scene& S, const double* x, const double* dir, const uint64_t* cand,
+                            int64_t n, uint8_t* flag, cudaStream_t st);
+bal_status launch_flag_below(const double* d, int64_t n, double thr, uint8_t* flag, cudaStream_t st);
 // A' dual update: s_i, mu_i += sigma b(d_i, dhat + s_i) for the device A' list.
 bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t st);
 
@@ -167,6 +172,11 @@ bal_status launch_dinv(Scene& S, cudaStream_t st);
 bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
 bal_status spmv32(Scene& S, const float* v, float* y, cudaStream_t st);
 bal_status make_f32_copy(Scene& S, cudaStream_t st);
+// order-preserving stream compaction of flagged entries (count read back)
+bal_status compact_u64(Scene& S, const uint64_t* in, const uint8_t* flag, int64_t n, uint64_t* out,
+                       int64_t* nsel, cudaStream_t st);
+bal_status compact_f64(Scene& S, const double* in, const uint8_t* flag, int64_t n, double* out,
+                       int64_t* nsel, cudaStream_t st);
 // S.scal[8] = ||b - y||^2, S.scal[9] = ||b||^2
 bal_status launch_residual_norm(Scene& S, const double* b, const double* y, cudaStream_t st);
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
