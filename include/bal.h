@@ -237,6 +237,27 @@ BAL_API bal_status bal_newton_step(bal_scene* scene, double* x_inout, bal_newton
 BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_inout,
                          bal_step_info* info, void* stream);
 
+/* ---- allocation-free solve (no counterpart in the paper) -------------------- */
+/* For callers that cannot allocate GPU memory while they run (a host
+ * application that owns all device memory, or a loop that forbids allocation
+ * after start-up): block-Jacobi PCG, same stopping rules as bal_pcg_solve
+ * (stagnation window 100), on a caller-provided symmetric block matrix
+ * H = D + L + L^T in DEVICE memory -- D [n_verts][9] diagonal blocks, nnz lower
+ * blocks (rows[nnz], cols[nnz] with rows > cols, vals[nnz][9] row-major) --
+ * solving H sol = rhs from the initial guess in sol (device, in/out). It calls
+ * no cudaMalloc / cudaFree: its working vectors live in a fixed device array
+ * of about 2.8 MB that every GPU loading the library keeps until exit, so
+ * n_verts may not exceed BAL_NOALLOC_MAX_VERTS (larger sizes return
+ * BAL_ERR_ARG). The first call on a device looks up that array's address and
+ * should come before any stream capture. All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+#define BAL_NOALLOC_MAX_VERTS 16384
+BAL_API bal_status bal_pcg_solve_noalloc(int32_t n_verts, const double* D, int64_t nnz,
+                                         const int32_t* rows, const int32_t* cols,
+                                         const double* vals, const double* rhs, double* sol,
+                                         double rel_tol, int32_t max_iter,
+                                         bal_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,8 @@ def load(path: str = LIB_PATH):
         "bal_energy": ([P, P, C.POINTER(C.c_double), P], C.c_int),
         "bal_newton_step": ([P, P, C.POINTER(NewtonInfo), P], C.c_int),
         "bal_time_step": ([P, P, P, C.POINTER(StepInfo), P], C.c_int),
+        "bal_pcg_solve_noalloc": ([C.c_int32, P, C.c_int64, P, P, P, P, P, C.c_double, C.c_int32,
+                                   C.POINTER(SolveInfo), P], C.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -337,6 +339,26 @@ class Scene:
         d = _as_dict(info)
         d["status"] = s
         return d
+
+
+NOALLOC_MAX_VERTS = 16384
+
+
+def pcg_solve_noalloc(D, rows, cols, vals, rhs, sol, rel_tol, max_iter, stream=None):
+    """Allocation-free PCG on caller-provided device arrays (see bal.h): for
+    callers that cannot allocate GPU memory while they run. D [nv*9], rows /
+    cols int32 [nnz] (rows > cols), vals [nnz*9], rhs / sol [nv*3]."""
+    import torch
+    nv = D.numel() // 9
+    nnz = rows.numel()
+    info = SolveInfo()
+    _check(load().bal_pcg_solve_noalloc(
+        int(nv), _dev(D, torch.float64), int(nnz),
+        _dev(rows, torch.int32) if nnz else None, _dev(cols, torch.int32) if nnz else None,
+        _dev(vals, torch.float64) if nnz else None, _dev(rhs, torch.float64, 3 * nv),
+        _dev(sol, torch.float64, 3 * nv), float(rel_tol), int(max_iter), C.byref(info),
+        _stream(stream)))
+    return _as_dict(info)
 
 
 def pair_key(kind, a, b):
