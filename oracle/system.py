@@ -178,3 +178,12 @@ def groups_from_lambda(lam):
     """e_j = sum of node j's three Lambda entries; group = floor(log10 e_j)."""
     e = lam.reshape(-1, 3).sum(axis=1)
     return e, np.floor(np.log10(e)).astype(np.int64)
+
+
+def masked_hessian(H, groups):
+    """H_dom of the warm start (Sec. 4.2.2): the assembled Hessian without the
+    entries that couple nodes of different stiffness groups."""
+    H = H.tocoo()
+    g = np.asarray(groups)
+    keep = g[H.row // 3] == g[H.col // 3]
+    return sp.coo_matrix((H.data[keep], (H.row[keep], H.col[keep])), shape=H.shape).tocsr()

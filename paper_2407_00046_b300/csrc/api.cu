@@ -679,6 +679,7 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dalloc(S, &S.pcg_q, 3 * (size_t)nv));
   TRYC(dalloc(S, &S.pcg_x, 3 * (size_t)nv));
   TRYC(dalloc(S, &S.pnorm, (size_t)nv));
+  TRYC(dalloc(S, &S.group, (size_t)nv));
   TRYC(dalloc(S, &S.D32, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.Dinv32, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.Lval32, 9 * (size_t)S.d.nnzL));

@@ -148,6 +148,7 @@ struct OffDiag {
   const int32_t* Ccol;
   const T* Cval;
   int64_t nC;
+  const int32_t* group;   // non-null: skip blocks whose row and column groups differ (Sec. 4.2.1)
 };
 
 // A symmetric block system: diagonal blocks, their inverses, off-diagonal blocks.
@@ -187,6 +188,7 @@ __global__ void k_spmv_offdiag(OffDiag<T> O, const T* __restrict__ v, T* __restr
     int i, j;
     const T* B;
     block_of(O, b, i, j, B);
+    if (O.group && O.group[i] != O.group[j]) continue;
     atomic_addv(y, i, mv(B, ldv(v, j)));
     atomic_addv(y, j, mtv(B, ldv(v, i)));
   }
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag<T> O, const T* __res
     int i, j;
     const T* B;
     block_of(O, b, i, j, B);
+    if (O.group && O.group[i] != O.group[j]) continue;
     const V3<T> pj = ldv(p, j), pi = ldv(p, i);
     const V3<T> bpj = mv(B, pj);
     atomic_addv(q, i, bpj);
@@ -363,6 +366,14 @@ __global__ void __launch_bounds__(NT) k_pcg_update(Sys<T> A, T* __restrict__ x,
   }
 }
 
+// group_j = floor(log10(e_j)), e_j = sum of node j's three Lambda entries (Sec. 4.2.2)
+__global__ void k_groups(const double* __restrict__ lam, int nv, int32_t* __restrict__ grp) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const double e = lam[3 * v] + lam[3 * v + 1] + lam[3 * v + 2];
+    grp[v] = (int32_t)floor(log10(e));
+  }
+}
+
 template <typename T>
 __global__ void k_convert(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -393,7 +404,7 @@ Sys<double> sys64(Scene& S) {
   A.D = S.d.D;
   A.Dinv = S.d.Dinv;
   A.O = OffDiag<double>{S.d.L_row, S.d.L_col, S.d.Lval, S.d.nnzL, S.C_row.as<int32_t>(),
-                        S.C_col.as<int32_t>(), S.C_val.as<double>(), S.nnzC};
+                        S.C_col.as<int32_t>(), S.C_val.as<double>(), S.nnzC, nullptr};
   A.nv = S.d.nv;
   return A;
 }
@@ -402,7 +413,7 @@ Sys<float> sys32(Scene& S) {
   A.D = S.D32;
   A.Dinv = S.Dinv32;
   A.O = OffDiag<float>{S.d.L_row, S.d.L_col, S.Lval32, S.d.nnzL, S.C_row.as<int32_t>(),
-                       S.C_col.as<int32_t>(), S.C_val32.as<float>(), S.nnzC};
+                       S.C_col.as<int32_t>(), S.C_val32.as<float>(), S.nnzC, nullptr};
   A.nv = S.d.nv;
   return A;
 }
@@ -639,9 +650,43 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
   return BAL_OK;
 }
 
+// Stiffness-grouped warm start (Sec. 4.2.2): block-Jacobi PCG on H_dom, the
+// Hessian without the blocks that couple different stiffness groups (a masked
+// SpMV), run to warm_tol or warm_max_iter from x; its result is x.
+static bal_status warm_start(Scene& S, const double* b, double* x, int* iters, int* ngroups,
+                             cudaStream_t st) {
+  k_groups<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d.Lambda, S.d.nv, S.group);
+  BAL_LAUNCH_CHECK();
+  Sys<double> A = sys64(S);
+  A.O.group = S.group;
+  BAL_TRY(spmv_t(A, x, S.pcg_q, st));
+  PcgScalars h;
+  BAL_TRY(pcg_core<double>(S, A, b, S.pcg_q, x, S.pcg_r, S.pcg_z, S.pcg_p, S.pcg_q, S.prm.warm_tol,
+                           S.prm.warm_max_iter, 1 << 30, &h, st));
+  *iters = h.it;
+  // number of distinct groups (min/max span) for the report
+  std::vector<int32_t> g(S.d.nv);
+  BAL_CUDA(cudaMemcpyAsync(g.data(), S.group, sizeof(int32_t) * S.d.nv, cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  std::vector<int32_t> u(g);
+  std::sort(u.begin(), u.end());
+  *ngroups = (int)(std::unique(u.begin(), u.end()) - u.begin());
+  return BAL_OK;
+}
+
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
                      bal_solve_info* info, cudaStream_t st) {
-  if (S.prm.precision == BAL_PREC_MIXED) return pcg_mixed(S, b, x, tol, max_it, info, st);
+  int witers = 0, ngroups = 0;
+  if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART && max_it > 0)
+    BAL_TRY(warm_start(S, b, x, &witers, &ngroups, st));
+  if (S.prm.precision == BAL_PREC_MIXED) {
+    BAL_TRY(pcg_mixed(S, b, x, tol, max_it, info, st));
+    if (info) {
+      info->warm_iters = witers;
+      info->n_groups = ngroups;
+    }
+    return BAL_OK;
+  }
   BAL_TRY(spmv(S, x, S.pcg_q, st));
   PcgScalars h;
   BAL_TRY(pcg_core<double>(S, sys64(S), b, S.pcg_q, x, S.pcg_r, S.pcg_z, S.pcg_p, S.pcg_q, tol,
@@ -651,8 +696,8 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
     info->stagnated = h.stagnated;
     info->converged = h.converged;
     info->refine_passes = 0;
-    info->warm_iters = 0;
-    info->n_groups = 0;
+    info->warm_iters = witers;
+    info->n_groups = ngroups;
     double rn, bn;
     BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
     info->rel_residual = bn > 0 ? rn / bn : rn;

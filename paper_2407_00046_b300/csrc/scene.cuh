@@ -100,6 +100,7 @@ struct Scene {
   double *xt = nullptr, *grad = nullptr, *gtmp = nullptr, *xtrial = nullptr, *dir = nullptr;
   double *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_x = nullptr;
   double* pnorm = nullptr;       // [nv] |p_v|
+  int32_t* group = nullptr;       // [nv] stiffness group of the warm start
   // bodies (connected components of the tet mesh)
   int32_t nbody = 0;
   int32_t* body = nullptr;        // [nv]

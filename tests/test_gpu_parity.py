@@ -202,3 +202,40 @@ def test_mixed_precision_trajectory_matches_oracle():
         xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8))
         assert info["converged"] == 1
         assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+
+
+def test_warm_start_solves_the_grouped_system(contact_case):
+    # warm start alone (global PCG given no iterations): the subdomain solve on
+    # H_dom (blocks coupling different floor(log10 e_j) groups removed)
+    import scipy.sparse.linalg as spla
+    sc, S, x = contact_case
+    S.set_al_state(3.0, 3.0)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    S.assemble_hessian(T(x), g)
+    m, y, ps = oracle_state(sc, x, 3.0)
+    H_or, lam = system.hessian(m, x, y, ps, 3.0, with_lambda=True)
+    e, grp = system.groups_from_lambda(lam)
+    frac = np.abs(np.log10(e) - np.round(np.log10(e)))
+    assert frac.min() > 1e-9          # no node sits on a group boundary
+    Hd = system.masked_hessian(H_or, grp)
+    b = -g
+    S.set_params(precond=bal.PRECOND_BJ_WARMSTART, warm_tol=1e-13, warm_max_iter=5000)
+    try:
+        sol = torch.zeros_like(b)
+        info = S.pcg_solve(b, sol, 1e-8, 0)
+        ref = spla.spsolve(Hd.tocsc(), b.cpu().numpy())
+        assert info["n_groups"] == len(np.unique(grp))
+        err = np.abs(sol.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < 1e-9, err
+        # full solve: warm start then global PCG to tolerance
+        S.set_params(warm_tol=1e-2, warm_max_iter=50)
+        sol.zero_()
+        info = S.pcg_solve(b, sol, 1e-9, 5000)
+        bn = b.cpu().numpy()
+        res = np.linalg.norm(bn - H_or @ sol.cpu().numpy()) / np.linalg.norm(bn)
+        assert info["converged"] == 1 and info["warm_iters"] > 0
+        # the global PCG tolerance is relative to its own r_0 (after the warm start)
+        r0_over_b = info["rel_residual"] / info["rel_residual_r0"]
+        assert res <= 1.05e-9 * max(1.0, r0_over_b), (res, info)
+    finally:
+        S.set_params(precond=bal.PRECOND_BJ)
