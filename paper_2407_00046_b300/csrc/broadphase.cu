@@ -3,12 +3,14 @@
 // axis-aligned boxes come within r of each other -- a superset of the pairs
 // with distance below r -- each pair exactly once, sorted by pair key.
 //
-// PT: triangles are inserted, with their box inflated by r, into every cell the
-// box overlaps; each surface vertex scans the one cell that contains it.
-// EE: edges are inserted the same way; each edge scans the cells overlapped by
-// its own (non-inflated) box and keeps a pair (e, f), f > e, only in the cell
-// that contains the lower corner of box(e) n inflated-box(f), so a pair found
-// in several cells is reported once.
+// Every primitive has an inflation radius r_P (uniform, or from its nodes'
+// displacements, see Grid). Triangles (for PT) and edges (for EE) are inserted,
+// with their boxes inflated by their own r, into every cell the box overlaps.
+// A query primitive (surface vertex, or edge e) scans the cells overlapped by
+// its own inflated box and keeps a pair only if the two inflated boxes overlap
+// and the cell holds the lower corner of their intersection, so a pair seen in
+// several cells is reported once. Large radii only enlarge their own
+// primitive's cell range, never the grid.
 // (The paper's broad phase is an LBVH, Sec. 5.3; the grid is this build's.)
 #include <cub/cub.cuh>
 
@@ -30,7 +32,7 @@ constexpr int64_t kMaxCellsPerPrim = 1 << 20;
 struct Grid {
   double inv_c;
   double half_r;     // uniform: r/2
-  double rmax;       // max r_v of this pass (triangles / edges are inserted inflated by r_P + rmax)
+  double rmax;       // typical r_v of this pass (sets the cell size only)
   int mode;
   const double* dir;
   const double* bmean;   // [nbody][3]
@@ -108,7 +110,7 @@ __global__ void k_count_cells(Dev S, const double* __restrict__ x, int kind, int
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int v[3], nv;
     prim_verts(S, kind, i, v, nv);
-    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv) + G.rmax);
+    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv));
     const int64_t c = (int64_t)(cell_of(b.hi.x, G.inv_c) - cell_of(b.lo.x, G.inv_c) + 1) *
                       (cell_of(b.hi.y, G.inv_c) - cell_of(b.lo.y, G.inv_c) + 1) *
                       (cell_of(b.hi.z, G.inv_c) - cell_of(b.lo.z, G.inv_c) + 1);
@@ -122,7 +124,7 @@ __global__ void k_fill_cells(Dev S, const double* __restrict__ x, int kind, int 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int v[3], nv;
     prim_verts(S, kind, i, v, nv);
-    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv) + G.rmax);
+    const Box b = inflate(prim_box(x, v, nv), prim_r(G, v, nv));
     const int x0 = cell_of(b.lo.x, G.inv_c), x1 = cell_of(b.hi.x, G.inv_c);
     const int y0 = cell_of(b.lo.y, G.inv_c), y1 = cell_of(b.hi.y, G.inv_c);
     const int z0 = cell_of(b.lo.z, G.inv_c), z1 = cell_of(b.hi.z, G.inv_c);
@@ -153,25 +155,37 @@ __device__ inline void emit(uint64_t* out, unsigned long long* counter, int64_t 
   if ((int64_t)idx < cap) out[idx] = key;
 }
 
+__device__ inline bool canonical(const Box& a, const Box& b, int ix, int iy, int iz, double inv_c) {
+  const d3 lo = d3{fmax(a.lo.x, b.lo.x), fmax(a.lo.y, b.lo.y), fmax(a.lo.z, b.lo.z)};
+  return cell_of(lo.x, inv_c) == ix && cell_of(lo.y, inv_c) == iy && cell_of(lo.z, inv_c) == iz;
+}
+
 __global__ void k_pt_query(Dev S, const double* __restrict__ x, Grid G,
                            const uint64_t* __restrict__ cells, const int32_t* __restrict__ ids,
                            int64_t ncell, uint64_t* out, unsigned long long* counter, int64_t cap) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.nsv; i += gridDim.x * blockDim.x) {
     const int v = S.surf[i];
     const d3 p = ld3(x, v);
-    const uint64_t key = cell_key(cell_of(p.x, G.inv_c), cell_of(p.y, G.inv_c), cell_of(p.z, G.inv_c));
-    for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
-      const int t = ids[k];
-      int tv[3], nv;
-      prim_verts(S, 0, t, tv, nv);
-      if (tv[0] == v || tv[1] == v || tv[2] == v) continue;
-      if (!body_ok(G, v, tv[0])) continue;
-      const Box b = inflate(prim_box(x, tv, 3), prim_r(G, tv, 3) + vert_r(G, v));
-      if (p.x < b.lo.x || p.x > b.hi.x || p.y < b.lo.y || p.y > b.hi.y || p.z < b.lo.z ||
-          p.z > b.hi.z)
-        continue;
-      emit(out, counter, cap, pair_key(0, (uint32_t)v, (uint32_t)t));
-    }
+    const double rv = vert_r(G, v);
+    const Box bp = Box{d3{p.x - rv, p.y - rv, p.z - rv}, d3{p.x + rv, p.y + rv, p.z + rv}};
+    const int x0 = cell_of(bp.lo.x, G.inv_c), x1 = cell_of(bp.hi.x, G.inv_c);
+    const int y0 = cell_of(bp.lo.y, G.inv_c), y1 = cell_of(bp.hi.y, G.inv_c);
+    const int z0 = cell_of(bp.lo.z, G.inv_c), z1 = cell_of(bp.hi.z, G.inv_c);
+    for (int ix = x0; ix <= x1; ++ix)
+      for (int iy = y0; iy <= y1; ++iy)
+        for (int iz = z0; iz <= z1; ++iz) {
+          const uint64_t key = cell_key(ix, iy, iz);
+          for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
+            const int t = ids[k];
+            int tv[3], nv;
+            prim_verts(S, 0, t, tv, nv);
+            if (tv[0] == v || tv[1] == v || tv[2] == v) continue;
+            if (!body_ok(G, v, tv[0])) continue;
+            const Box bt = inflate(prim_box(x, tv, 3), prim_r(G, tv, 3));
+            if (!overlap(bp, bt) || !canonical(bp, bt, ix, iy, iz, G.inv_c)) continue;
+            emit(out, counter, cap, pair_key(0, (uint32_t)v, (uint32_t)t));
+          }
+        }
   }
 }
 
@@ -181,8 +195,7 @@ __global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.ne; e += gridDim.x * blockDim.x) {
     int ev[3], nv;
     prim_verts(S, 1, e, ev, nv);
-    const Box be = prim_box(x, ev, 2);
-    const double re = prim_r(G, ev, 2);
+    const Box be = inflate(prim_box(x, ev, 2), prim_r(G, ev, 2));
     const int x0 = cell_of(be.lo.x, G.inv_c), x1 = cell_of(be.hi.x, G.inv_c);
     const int y0 = cell_of(be.lo.y, G.inv_c), y1 = cell_of(be.hi.y, G.inv_c);
     const int z0 = cell_of(be.lo.z, G.inv_c), z1 = cell_of(be.hi.z, G.inv_c);
@@ -197,15 +210,8 @@ __global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
             prim_verts(S, 1, f, fv, nv);
             if (fv[0] == ev[0] || fv[0] == ev[1] || fv[1] == ev[0] || fv[1] == ev[1]) continue;
             if (!body_ok(G, ev[0], fv[0])) continue;
-            const Box bf0 = prim_box(x, fv, 2);
-            const double rf = prim_r(G, fv, 2);
-            if (!overlap(inflate(be, re), inflate(bf0, rf))) continue;
-            // canonical cell: lower corner of box(e) n (box(f) inflated as inserted)
-            const Box bf = inflate(bf0, rf + G.rmax);
-            const d3 lo = d3{fmax(be.lo.x, bf.lo.x), fmax(be.lo.y, bf.lo.y), fmax(be.lo.z, bf.lo.z)};
-            if (cell_of(lo.x, G.inv_c) != ix || cell_of(lo.y, G.inv_c) != iy ||
-                cell_of(lo.z, G.inv_c) != iz)
-              continue;
+            const Box bf = inflate(prim_box(x, fv, 2), prim_r(G, fv, 2));
+            if (!overlap(be, bf) || !canonical(be, bf, ix, iy, iz, G.inv_c)) continue;
             emit(out, counter, cap, pair_key(1, (uint32_t)e, (uint32_t)f));
           }
         }
@@ -267,17 +273,17 @@ __global__ void k_body_div(double* bsum, const double* __restrict__ inv_cnt, int
   }
 }
 template <int NT>
-__global__ void __launch_bounds__(NT) k_rmax(Dev S, Grid G, double* partials) {
+__global__ void __launch_bounds__(NT) k_rsum(Dev S, Grid G, double* partials) {
   double m = 0.0;
-  for (int v = blockIdx.x * NT + threadIdx.x; v < S.nv; v += gridDim.x * NT) m = fmax(m, vert_r(G, v));
-  m = block_max<double, NT>(m, 0.0);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < S.nsv; i += gridDim.x * NT) m += vert_r(G, S.surf[i]);
+  m = block_sum<double, NT>(m);
   if (threadIdx.x == 0) partials[blockIdx.x] = m;
 }
 
 // one grid pass appending to out (counter not reset here)
 bal_status grid_pass(Scene& S, const double* x, Grid& G, Buf& out, int64_t cap,
                      unsigned long long* counter, cudaStream_t st) {
-  G.inv_c = 1.0 / (4.0 * G.rmax + 1.5 * S.mean_edge);
+  G.inv_c = 1.0 / (2.0 * G.rmax + 1.5 * S.mean_edge);
   int64_t ncell = 0;
   uint64_t* cells = nullptr;
   int32_t* ids = nullptr;
@@ -340,7 +346,7 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
   Grid G{};
   G.mode = 0;
   G.half_r = 0.5 * r;
-  G.rmax = 0.5 * r;
+  G.rmax = 0.5 * r;   // (uniform radius)
   return collect(S, x, &G, 1, out, alt, n, st);
 }
 
@@ -362,15 +368,16 @@ bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, 
     P[k].eta = S.prm.step_bound;
     P[k].base = 0.5 * S.d.dhat;
     constexpr int NT = 256;
-    k_rmax<NT><<<2 * kNumSM, NT, 0, st>>>(S.d, P[k], S.partials);
+    k_rsum<NT><<<2 * kNumSM, NT, 0, st>>>(S.d, P[k], S.partials);
     BAL_LAUNCH_CHECK();
-    BAL_TRY(finish_reduce(S, 2 * kNumSM, 15 + k, RED_MAX, st));
+    BAL_TRY(finish_reduce(S, 2 * kNumSM, 15 + k, RED_SUM, st));
   }
   double rm[2];
   BAL_CUDA(cudaMemcpyAsync(rm, S.scal + 15, sizeof(rm), cudaMemcpyDeviceToHost, st));
   BAL_CUDA(cudaStreamSynchronize(st));
-  P[0].rmax = rm[0];
-  P[1].rmax = rm[1];
+  // rmax holds the mean surface radius: it only sets the cell size
+  P[0].rmax = S.d.nsv ? rm[0] / S.d.nsv : S.d.dhat;
+  P[1].rmax = S.d.nsv ? rm[1] / S.d.nsv : S.d.dhat;
   const int npass = S.nbody > 1 ? 2 : 1;
   return collect(S, x, P, npass, out, alt, n, st);
 }

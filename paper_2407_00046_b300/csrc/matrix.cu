@@ -16,8 +16,9 @@
 // blocks into q and partial sums of 2 p_i^T L_ij p_j, the last CTA turning
 // p.q = p^T H p into alpha; (3) x += alpha p, r -= alpha q, z = D^{-1} r and
 // partial sums of r.z, r.r, the last CTA deciding convergence (||r|| <= tol
-// ||r_0||), stagnation (no new minimum of ||r|| in `window` iterations) and
-// beta. Once `done` is set the remaining launches of a chunk return at once, so
+// ||r_0||), stagnation (no new minimum of the preconditioned residual
+// sqrt(r.z) in `window` iterations: ||r||_2 of CG on a stiff system can rise
+// for hundreds of iterations while the iterate improves) and beta. Once `done` is set the remaining launches of a chunk return at once, so
 // the host only synchronises once per chunk of iterations.
 #include <cub/cub.cuh>
 
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(NT) k_pcg_init(Sys<T> A, const T* __restrict__
       P->r0norm = sqrt(trr);
       P->rnorm = P->r0norm;
       P->bnorm = sqrt(tbb);
-      P->best = P->r0norm;
+      P->best = sqrt(fmax(trz, 0.0));
       P->best_it = 0;
       P->it = 0;
       P->tol_abs = tol * P->r0norm;
@@ -342,10 +343,11 @@ __global__ void __launch_bounds__(NT) k_pcg_update(Sys<T> A, T* __restrict__ x,
     if (threadIdx.x == 0) {
       const int it = P->it + 1;
       const double rn = sqrt(trr);
+      const double pn = sqrt(fmax(trz, 0.0));   // preconditioned residual norm
       P->it = it;
       P->rnorm = rn;
-      if (rn < P->best) {
-        P->best = rn;
+      if (pn < P->best) {
+        P->best = pn;
         P->best_it = it;
       }
       if (!isfinite(rn)) {
@@ -677,7 +679,7 @@ static bal_status warm_start(Scene& S, const double* b, double* x, int* iters, i
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
                      bal_solve_info* info, cudaStream_t st) {
   int witers = 0, ngroups = 0;
-  if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART && max_it > 0)
+  if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART)
     BAL_TRY(warm_start(S, b, x, &witers, &ngroups, st));
   if (S.prm.precision == BAL_PREC_MIXED) {
     BAL_TRY(pcg_mixed(S, b, x, tol, max_it, info, st));
