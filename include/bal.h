@@ -73,6 +73,9 @@ typedef struct {
   int32_t mixed_inner_max;    /* FP32 inner PCG iterations per refinement pass */
   double mixed_inner_tol;     /* FP32 inner relative tolerance per pass */
   int32_t mixed_max_refine;   /* max FP64 refinement passes */
+  int32_t ca_max_iter;        /* step bound: conservative-advancement iterations per pair (64) */
+  int32_t freeze_al;          /* 1: hold sigma, A', mu fixed (no dual update, no sigma schedule,
+                                 no A' rule) -- the map the adjoint differentiates */
 } bal_params;
 
 /* Scene description: HOST arrays, copied by bal_create_scene. */
@@ -137,6 +140,8 @@ typedef struct {
   int32_t refine_passes;      /* mixed precision: FP64 refinement passes */
   int32_t warm_iters;         /* warm start: subdomain PCG iterations */
   int32_t n_groups;           /* warm start: stiffness groups */
+  int32_t negative_curvature; /* adjoint: 1 if the unprojected H was indefinite and the
+                                 projected H was used instead */
 } bal_solve_info;
 
 typedef struct {
@@ -257,6 +262,28 @@ BAL_API bal_status bal_pcg_solve_noalloc(int32_t n_verts, const double* D, int64
                                          const double* vals, const double* rhs, double* sol,
                                          double rel_tol, int32_t max_iter,
                                          bal_solve_info* info, void* stream);
+
+/* ---- adjoint of the time step (not in the paper) ----------------------------- */
+/* Replaces per-tet Young's modulus and Poisson ratio (HOST arrays [n_tets]). */
+BAL_API bal_status bal_set_materials(bal_scene* scene, const double* E, const double* nu);
+
+/* Adjoint of one time step x_{t+1} = argmin L_sigma(x; x_t, v_t, E) with the
+ * converged AL state `al` (sigma, A', mu of the step's last iteration) held
+ * fixed: differentiating grad_x L(x_{t+1}) = 0 gives H lambda = a with H the
+ * UNPROJECTED Hessian at x_{t+1} and a = dL/dx_{t+1} + dL/dv_{t+1} / h
+ * (v_{t+1} = (x_{t+1} - x_t)/h). Then, on free vertices,
+ *   dL/dx_t = M lambda / h^2 - dL/dv_{t+1} / h,   dL/dv_t = M lambda / h,
+ * (pinned entries are zero) and dL/dE_e += -lambda_e^T grad W_e / E_e (mu and
+ * lam are linear in E). If PCG finds H indefinite it falls back to the
+ * projected H and sets info->negative_curvature. All vectors are DEVICE
+ * [n_verts*3]; dLdE_accum is DEVICE [n_tets] (accumulated). Overwrites the
+ * scene's current step state (y, A', mu, sigma). */
+BAL_API bal_status bal_adjoint_step(bal_scene* scene, const double* x_t, const double* v_t,
+                                    const double* x_next, const bal_al_state* al,
+                                    const double* dLdx_next, const double* dLdv_next,
+                                    double* dLdx_prev, double* dLdv_prev, double* dLdE_accum,
+                                    double rel_tol, int32_t max_iter, bal_solve_info* info,
+                                    void* stream);
 
 #ifdef __cplusplus
 }

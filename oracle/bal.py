@@ -20,10 +20,12 @@ paper used here (each one is recorded in the design notes):
 * sigma0 = -(sum grad b)^T grad E / ||sum grad b||^2 over A at x_0 (the
   printed denominator is not squared, which is not dimensionally
   consistent), floored at mbar / (h^2 b''(dhat/2, dhat));
-* line search: alpha_0 = min(1, min over pairs of 0.9 d_i / Delta_i) where
-  Delta_i = max |p_a - p_b| over a node of each primitive bounds how fast the
-  pair can close along p (a rigid translation closes nothing); the candidate
-  radius dhat + 2 max|p_v| / 0.9 contains every pair that can constrain alpha or
+* line search: alpha_0 = the largest t <= 1 along x + t p over which every pair
+  keeps 10% of its current distance, found per pair by conservative
+  advancement with Delta_i = max |p_a - p_b| over a node of each primitive as
+  the bound on how fast the pair can close (an additive-CCD style time of
+  impact in place of the paper's cubic CCD, Sec. 5.3); the candidate radius
+  dhat + 2 max|p_v| / 0.9 contains every pair that can constrain alpha or
   enter A during the step; halve until no tet is
   inverted, the number of active pairs is within the memory cap (Sec. 5.2),
   and L_sigma does not increase by more than a rounding slack.
@@ -35,7 +37,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
-from . import barrier, contact, elastic
+from . import barrier, contact, distance, elastic
 from .system import PairSet, energy_parts, gradient, hessian, inertia_target
 
 
@@ -52,6 +54,8 @@ class Params:
     ls_min_alpha: float = 1e-9      # App. B
     ls_slack: float = 1e-12
     contact_cap: int = 1 << 30      # Sec. 5.2 memory limit on |A|
+    ca_max_iter: int = 64           # conservative-advancement iterations per pair
+    freeze_al: bool = False         # hold sigma, A', mu fixed (adjoint checks)
 
 
 def sigma_floor(model):
@@ -109,19 +113,52 @@ def displacement_bound(pairs, p, scene):
     return np.where(is_pt, pt, ee)
 
 
+def step_bound(model, x, p, pairs, prm: Params):
+    """Largest alpha <= 1 along x + t p over which every pair keeps at least
+    (1 - step_bound) of its current distance d0, by conservative advancement:
+    d can shrink by at most Delta per unit t (Delta = max |p_a - p_b|), so from t
+    with distance d(t) it is safe to advance by (d(t) - (1 - eta) d0) / Delta.
+    Iterate until the target distance is reached (the time of impact of the
+    offset surface) or t = 1, at most ca_max_iter times per pair."""
+    if not pairs:
+        return 1.0
+    sc = model.scene
+    eta = prm.step_bound
+    d0, _, _ = contact.pair_distances(x, pairs, sc)
+    Dl = displacement_bound(pairs, p, sc)
+    m = eta * d0 < Dl
+    if not np.any(m):
+        return 1.0
+    keys = [k for k, f in zip(pairs, m) if f]
+    d0, Dl = d0[m], Dl[m]
+    goal = (1.0 - eta) * d0
+    nodes = contact.stencil_nodes(keys, sc)
+    X0, P0 = x[nodes], p[nodes]                         # [n,4,3]
+    is_ee = np.asarray(keys, dtype=np.int64).reshape(-1, 3)[:, 0] == 1
+    t = np.zeros(len(keys))
+    active = np.ones(len(keys), dtype=bool)
+    for _ in range(prm.ca_max_iter):
+        idx = np.flatnonzero(active)
+        if idx.size == 0:
+            break
+        X4 = X0[idx] + t[idx, None, None] * P0[idx]
+        dk = distance.distances(X4, distance.classify(X4, is_ee[idx]))
+        step = (dk - goal[idx]) / Dl[idx]
+        done_toi = step <= 1e-6 * np.maximum(t[idx], 1e-3)
+        newt = t[idx] + step
+        reach = newt >= 1.0
+        t[idx] = np.where(done_toi, t[idx], np.minimum(newt, 1.0))
+        active[idx] = ~(done_toi | reach)
+    return float(min(1.0, t.min()))
+
+
 def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
     sc = model.scene
     pnorm = np.sqrt(np.sum(p * p, axis=1))
     delta = float(pnorm[sc.surf_verts].max()) if sc.surf_verts.size else 0.0
     r = model.dhat + 2.0 * delta / prm.step_bound
     cand = contact.candidate_pairs(x, sc, r)
-    alpha = 1.0
-    if cand:
-        d0, _, _ = contact.pair_distances(x, cand, sc)
-        Dl = displacement_bound(cand, p, sc)
-        m = prm.step_bound * d0 < Dl
-        if np.any(m):
-            alpha = min(1.0, float(np.min(prm.step_bound * d0[m] / Dl[m])))
+    alpha = step_bound(model, x, p, cand, prm)
     parts_old = energy_parts(model, x, y, ps, sigma)
     E_old = sum(parts_old)
     slack = prm.ls_slack * sum(abs(t) for t in parts_old)
@@ -165,15 +202,19 @@ def solve(H, rhs):
     return spla.splu(H.tocsc()).solve(rhs)
 
 
-def time_step(model, x_t, v_t, prm: Params = Params(), log=None):
-    """One BAL time step from (x_t, v_t). Returns (x_{t+1}, v_{t+1}, info)."""
+def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
+    """One BAL time step from (x_t, v_t). Returns (x_{t+1}, v_{t+1}, info).
+    frozen = (sigma, {A' key: mu}) holds the AL state fixed (no dual update, no
+    sigma schedule, no A' rule): the map the adjoint differentiates."""
     dh = model.dhat
     y = inertia_target(model, x_t, v_t)
     x = np.array(x_t, dtype=np.float64, copy=True)
     A_keys, A_d = active_pairs(model, x)
-    sigma0 = initial_sigma(model, x, y, A_keys)
+    if frozen is not None:
+        sigma0, Ap = frozen[0], dict(frozen[1])
+    else:
+        sigma0, Ap = initial_sigma(model, x, y, A_keys), {}
     sigma = sigma0
-    Ap = {}
     dmin_prev = math.inf
     info = dict(sigma0=sigma0, iters=0, converged=False, ls_failed=False, log=[])
     e0 = None
@@ -181,7 +222,7 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None):
         if l > 0:
             A_keys, A_d = active_pairs(model, x)
         dmin = float(A_d.min()) if A_d.size else math.inf
-        if l > 0:
+        if l > 0 and frozen is None:
             # dual update of the previous iteration, evaluated at x^[l]
             if Ap:
                 keys = sorted(Ap)
@@ -196,7 +237,9 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None):
                 else:
                     sigma = min(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
         # augmentation set rule (Alg. 1 lines 3-6)
-        if dmin > prm.ap_ratio * dh:
+        if frozen is not None:
+            pass
+        elif dmin > prm.ap_ratio * dh:
             Ap = {}
         elif dmin < dmin_prev or not Ap:
             Ap = {k: Ap.get(k, 0.0) for k, dd in zip(A_keys, A_d) if dd < prm.ap_ratio * dh}

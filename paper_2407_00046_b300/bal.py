@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("contact_cap", C.c_int64), ("ls_extra_pcg", C.c_int32),
                 ("warm_tol", C.c_double), ("warm_max_iter", C.c_int32),
                 ("mixed_inner_max", C.c_int32), ("mixed_inner_tol", C.c_double),
-                ("mixed_max_refine", C.c_int32)]
+                ("mixed_max_refine", C.c_int32), ("ca_max_iter", C.c_int32),
+                ("freeze_al", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -68,7 +69,8 @@ class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("rel_residual", C.c_double),
                 ("rel_residual_r0", C.c_double), ("stagnated", C.c_int32),
                 ("converged", C.c_int32), ("refine_passes", C.c_int32),
-                ("warm_iters", C.c_int32), ("n_groups", C.c_int32)]
+                ("warm_iters", C.c_int32), ("n_groups", C.c_int32),
+                ("negative_curvature", C.c_int32)]
 
 
 class NewtonInfo(C.Structure):
@@ -126,6 +128,9 @@ def load(path: str = LIB_PATH):
         "bal_energy": ([P, P, C.POINTER(C.c_double), P], C.c_int),
         "bal_newton_step": ([P, P, C.POINTER(NewtonInfo), P], C.c_int),
         "bal_time_step": ([P, P, P, C.POINTER(StepInfo), P], C.c_int),
+        "bal_set_materials": ([P, P, P], C.c_int),
+        "bal_adjoint_step": ([P, P, P, P, C.POINTER(ALState), P, P, P, P, P, C.c_double, C.c_int32,
+                              C.POINTER(SolveInfo), P], C.c_int),
         "bal_pcg_solve_noalloc": ([C.c_int32, P, C.c_int64, P, P, P, P, P, C.c_double, C.c_int32,
                                    C.POINTER(SolveInfo), P], C.c_int),
     }
@@ -327,6 +332,33 @@ class Scene:
         _check(load().bal_newton_step(self._h, _dev(x, torch.float64, 3 * self.nv), C.byref(info),
                                       _stream(stream)))
         return _as_dict(info)
+
+    def set_materials(self, E, nu=None):
+        """Per-tet Young's modulus (and Poisson ratio) from host arrays."""
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64))
+        nu = np.ascontiguousarray(np.asarray(self._keep["nu"] if nu is None else nu, dtype=np.float64))
+        _check(load().bal_set_materials(self._h, E.ctypes.data_as(P), nu.ctypes.data_as(P)))
+        self._keep["E"], self._keep["nu"] = E, nu
+
+    def adjoint_step(self, x_t, v_t, x_next, al, dLdx_next, dLdv_next, dLdE_accum,
+                     rel_tol=1e-12, max_iter=100000, stream=None):
+        """One step of the adjoint: returns (dL/dx_t, dL/dv_t, info); adds into dLdE_accum."""
+        import torch
+        n = 3 * self.nv
+        keys = np.ascontiguousarray(np.asarray(al["ap_keys"], dtype=np.uint64))
+        mu = np.ascontiguousarray(np.asarray(al["ap_mu"], dtype=np.float64))
+        st = ALState(al["sigma"], al["sigma0"], al.get("dmin_prev", float("inf")), len(keys),
+                     keys.ctypes.data if len(keys) else None, mu.ctypes.data if len(mu) else None)
+        dx = torch.empty_like(dLdx_next)
+        dv = torch.empty_like(dLdv_next)
+        info = SolveInfo()
+        _check(load().bal_adjoint_step(
+            self._h, _dev(x_t, torch.float64, n), _dev(v_t, torch.float64, n),
+            _dev(x_next, torch.float64, n), C.byref(st), _dev(dLdx_next, torch.float64, n),
+            _dev(dLdv_next, torch.float64, n), _dev(dx, torch.float64, n), _dev(dv, torch.float64, n),
+            _dev(dLdE_accum, torch.float64, self.src.n_tets), float(rel_tol), int(max_iter),
+            C.byref(info), _stream(stream)))
+        return dx, dv, _as_dict(info)
 
     def time_step(self, x, v, stream=None, check=True):
         import torch

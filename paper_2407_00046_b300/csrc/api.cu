@@ -292,7 +292,7 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   BAL_TRY(detect_active(S, x, A, Ad, st));
   double dmin = INFINITY;
   for (double d : Ad) dmin = std::min(dmin, d);
-  if (S.l > 0) {
+  if (S.l > 0 && !S.prm.freeze_al) {
     // dual update of the previous iteration, evaluated at x^[l] (Alg. 1 lines 12-15)
     if (!S.ap_keys.empty()) {
       BAL_TRY(upload_ap(S, st));
@@ -309,7 +309,9 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
     }
   }
   // augmentation set rule (Alg. 1 lines 3-6); mu kept for pairs staying in A'
-  if (dmin > thr) {
+  if (S.prm.freeze_al) {
+    // A', mu and sigma held fixed
+  } else if (dmin > thr) {
     S.ap_keys.clear();
     S.ap_mu.clear();
   } else if (dmin < S.dmin_prev || S.ap_keys.empty()) {
@@ -436,6 +438,29 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   return BAL_OK;
 }
 
+// a = dL/dx_{t+1} + dL/dv_{t+1} / h on free vertices, 0 on pinned ones
+__global__ void k_adj_rhs(Dev S, const double* __restrict__ gx, const double* __restrict__ gv,
+                          double* __restrict__ a) {
+  const double ih = 1.0 / S.h;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x)
+    st3(a, v, S.pinned[v] ? d3{0, 0, 0} : ld3(gx, v) + ih * ld3(gv, v));
+}
+// dL/dx_t = M lam / h^2 - dL/dv_{t+1} / h, dL/dv_t = M lam / h on free vertices
+__global__ void k_adj_out(Dev S, const double* __restrict__ lam, const double* __restrict__ gv,
+                          double* __restrict__ dx, double* __restrict__ dv) {
+  const double ih = 1.0 / S.h;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x) {
+    if (S.pinned[v]) {
+      st3(dx, v, d3{0, 0, 0});
+      st3(dv, v, d3{0, 0, 0});
+      continue;
+    }
+    const d3 ml = S.mass[v] * ld3(lam, v);
+    st3(dx, v, (ih * ih) * ml - ih * ld3(gv, v));
+    st3(dv, v, ih * ml);
+  }
+}
+
 __global__ void k_velocity(int64_t n, double ih, const double* __restrict__ x,
                            const double* __restrict__ xt, double* __restrict__ v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -477,6 +502,8 @@ void bal_default_params(bal_params* p) {
   p->mixed_inner_max = 200;
   p->mixed_inner_tol = 1e-3;
   p->mixed_max_refine = 20;
+  p->ca_max_iter = 64;
+  p->freeze_al = 0;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -654,6 +681,9 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dupload(S, &S.d.Dm_inv, (const double*)Dmi.data(), Dmi.size()));
   TRYC(dupload(S, &S.d.vol, (const double*)vol.data(), vol.size()));
   TRYC(dupload(S, &S.d.mu, (const double*)mu.data(), mu.size()));
+  S.E_h.assign(desc->E, desc->E + nt);
+  S.nu_h.assign(desc->nu, desc->nu + nt);
+  TRYC(dupload(S, (const double**)&S.E, (const double*)S.E_h.data(), S.E_h.size()));
   TRYC(dupload(S, &S.d.lam, (const double*)lam.data(), lam.size()));
   TRYC(dupload(S, &S.d.mass, (const double*)mass.data(), mass.size()));
   TRYC(dupload(S, &S.d.L_row_ptr, (const int32_t*)S.row_ptr_h.data(), S.row_ptr_h.size()));
@@ -772,11 +802,13 @@ bal_status bal_step_begin(bal_scene* sc, const double* x_t, const double* v_t, v
   const int64_t n3 = 3 * (int64_t)S.d.nv;
   BAL_CUDA(cudaMemcpyAsync(S.xt, x_t, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
   BAL_TRY(launch_make_y(S, x_t, v_t, S.d.y, st));
-  S.ap_keys.clear();
-  S.ap_mu.clear();
   S.dmin_prev = INFINITY;
   S.l = 0;
   S.e0 = 0.0;
+  S.step_active = true;
+  if (S.prm.freeze_al) return BAL_OK;   // keep sigma, A', mu as set by bal_set_al_state
+  S.ap_keys.clear();
+  S.ap_mu.clear();
   std::vector<uint64_t> A;
   std::vector<double> Ad;
   BAL_TRY(detect_active(S, x_t, A, Ad, st));
@@ -785,7 +817,6 @@ bal_status bal_step_begin(bal_scene* sc, const double* x_t, const double* v_t, v
   BAL_TRY(initial_sigma(S, x_t, A, &s0, st));
   S.sigma0 = s0;
   S.sigma = s0;
-  S.step_active = true;
   return BAL_OK;
 }
 
@@ -945,6 +976,78 @@ bal_status bal_newton_step(bal_scene* sc, double* x, bal_newton_info* info, void
     return BAL_ERR_STATE;
   }
   return newton_iteration(sc->S, x, info, (cudaStream_t)stream);
+}
+
+bal_status bal_set_materials(bal_scene* sc, const double* E, const double* nu) {
+  BAL_TRY(check_scene(sc));
+  if (!E || !nu) return BAL_ERR_ARG;
+  Scene& S = sc->S;
+  const int nt = S.d.nt;
+  std::vector<double> mu(nt), lam(nt);
+  for (int t = 0; t < nt; ++t) {
+    if (!(E[t] > 0) || !(nu[t] > -1 && nu[t] < 0.5)) {
+      set_error("bal_set_materials: invalid E or nu at tet %d", t);
+      return BAL_ERR_ARG;
+    }
+    mu[t] = E[t] / (2.0 * (1.0 + nu[t]));
+    lam[t] = E[t] * nu[t] / ((1.0 + nu[t]) * (1.0 - 2.0 * nu[t]));
+  }
+  S.E_h.assign(E, E + nt);
+  S.nu_h.assign(nu, nu + nt);
+  BAL_CUDA(cudaMemcpy((void*)S.d.mu, mu.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
+  BAL_CUDA(cudaMemcpy((void*)S.d.lam, lam.data(), sizeof(double) * nt, cudaMemcpyHostToDevice));
+  BAL_CUDA(cudaMemcpy(S.E, E, sizeof(double) * nt, cudaMemcpyHostToDevice));
+  return BAL_OK;
+}
+
+bal_status bal_adjoint_step(bal_scene* sc, const double* x_t, const double* v_t, const double* x_next,
+                            const bal_al_state* al, const double* gx, const double* gv, double* dx,
+                            double* dv, double* dE, double rel_tol, int32_t max_iter,
+                            bal_solve_info* info, void* stream) {
+  BAL_TRY(check_scene(sc));
+  if (!x_t || !v_t || !x_next || !al || !gx || !gv || !dx || !dv || !dE || !(rel_tol >= 0) ||
+      max_iter < 0) {
+    set_error("bal_adjoint_step: invalid argument");
+    return BAL_ERR_ARG;
+  }
+  Scene& S = sc->S;
+  cudaStream_t st = (cudaStream_t)stream;
+  BAL_TRY(launch_make_y(S, x_t, v_t, S.d.y, st));
+  BAL_TRY(bal_set_al_state(sc, al));
+  S.step_active = true;
+  std::vector<uint64_t> A;
+  std::vector<double> Ad;
+  BAL_TRY(detect_active(S, x_next, A, Ad, st));
+  BAL_TRY(build_eval(S, x_next, A, st));
+  const int64_t n3 = 3 * (int64_t)S.d.nv;
+  k_adj_rhs<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, gx, gv, S.gtmp);
+  BAL_LAUNCH_CHECK();
+  bal_solve_info si;
+  std::memset(&si, 0, sizeof(si));
+  S.project = false;
+  bal_status s = assemble(S, x_next, nullptr, st);
+  S.project = true;
+  BAL_TRY(s);
+  BAL_CUDA(cudaMemsetAsync(S.dir, 0, sizeof(double) * n3, st));
+  const int32_t keep_precond = S.prm.precond, keep_prec = S.prm.precision;
+  S.prm.precond = BAL_PRECOND_BJ;
+  S.prm.precision = BAL_PREC_FP64;
+  s = pcg_solve(S, S.gtmp, S.dir, rel_tol, max_iter, &si, st);
+  if (s == BAL_ERR_NAN) {   // indefinite: fall back to the projected Hessian
+    BAL_TRY(assemble(S, x_next, nullptr, st));
+    BAL_CUDA(cudaMemsetAsync(S.dir, 0, sizeof(double) * n3, st));
+    s = pcg_solve(S, S.gtmp, S.dir, rel_tol, max_iter, &si, st);
+    si.negative_curvature = 1;
+  }
+  S.prm.precond = keep_precond;
+  S.prm.precision = keep_prec;
+  BAL_TRY(s);
+  k_adj_out<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.dir, gv, dx, dv);
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(launch_dLdE(S, x_next, S.dir, dE, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  if (info) *info = si;
+  return BAL_OK;
 }
 
 bal_status bal_time_step(bal_scene* sc, double* x, double* v, bal_step_info* info, void* stream) {

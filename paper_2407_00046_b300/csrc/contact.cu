@@ -375,6 +375,7 @@ struct ContactArgs {
   int hess;
   uint64_t* emit_keys;   // [n][6]
   double* emit_vals;     // [n][6][9]
+  int project;           // 0: emit the unprojected stencil Hessian (adjoint)
 };
 
 __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __restrict__ x,
@@ -437,19 +438,24 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
         const double m = 0.5 * (H[12 * r + c] + H[12 * c + r]);
         H[12 * r + c] = H[12 * c + r] = m;
       }
-    jacobi12(H, Q);
-    double lam[12], tr = 0.0;
-    for (int k = 0; k < 12; ++k) {
-      lam[k] = H[13 * k] > 0.0 ? H[13 * k] : 0.0;
-      tr += lam[k];
+    double tr = 0.0;
+    if (A.project) {
+      jacobi12(H, Q);
+      double lam[12];
+      for (int k = 0; k < 12; ++k) {
+        lam[k] = H[13 * k] > 0.0 ? H[13 * k] : 0.0;
+        tr += lam[k];
+      }
+      for (int r = 0; r < 12; ++r)
+        for (int c = r; c < 12; ++c) {
+          double acc = 0.0;
+          for (int k = 0; k < 12; ++k) acc += Q[12 * r + k] * lam[k] * Q[12 * c + k];
+          H[12 * r + c] = H[12 * c + r] = acc;
+        }
+    } else {
+      for (int k = 0; k < 12; ++k) tr += H[13 * k];
     }
     tr *= (1.0 / 12.0);
-    for (int r = 0; r < 12; ++r)
-      for (int c = r; c < 12; ++c) {
-        double acc = 0.0;
-        for (int k = 0; k < 12; ++k) acc += Q[12 * r + k] * lam[k] * Q[12 * c + k];
-        H[12 * r + c] = H[12 * c + r] = acc;
-      }
 #pragma unroll
     for (int nd = 0; nd < 4; ++nd) {
       atomicAdd(S.Lambda + 3 * v[nd], tr);
@@ -526,19 +532,23 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
   }
 }
 
+// Step bound by conservative advancement: along x + t p a pair's distance can
+// shrink by at most Delta per unit t (Delta = max |p_a - p_b| over a node of
+// each primitive), so from t it is safe to advance by (d(t) - (1 - eta) d0) /
+// Delta. Iterate to the time at which the distance would reach (1 - eta) d0,
+// or to t = 1, at most max_iter times; the block minimum of t goes to partials.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restrict__ x,
                                                    const double* __restrict__ dir,
                                                    const uint64_t* __restrict__ cand, int64_t nc,
-                                                   double eta, double* partials) {
+                                                   double eta, int max_iter, double* partials) {
   double amin = 1.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
     int v[4];
     d3 X[4];
     Region R;
     const uint64_t key = cand[i];
-    const double d = pair_distance(S, x, key, v, X, R);
-    // largest relative node displacement across the pair
+    const double d0 = pair_distance(S, x, key, v, X, R);
     d3 P[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) P[a] = ld3(dir, v[a]);
@@ -549,7 +559,27 @@ __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restri
         const d3 w = P[a] - P[b];
         Dl = fmax(Dl, sqrt(dot(w, w)));
       }
-    if (eta * d < Dl) amin = fmin(amin, eta * d / Dl);
+    if (!(eta * d0 < Dl)) continue;
+    const double goal = (1.0 - eta) * d0;
+    double t = 0.0;
+    for (int it = 0; it < max_iter; ++it) {
+      d3 Xt[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        Xt[a] = d3{__dadd_rn(X[a].x, __dmul_rn(t, P[a].x)), __dadd_rn(X[a].y, __dmul_rn(t, P[a].y)),
+                   __dadd_rn(X[a].z, __dmul_rn(t, P[a].z))};
+      const Region Rt = key_kind(key) == 0 ? classify_pt(Xt) : classify_ee(Xt);
+      const double dk = region_distance(Xt, Rt);
+      const double step = (dk - goal) / Dl;
+      if (step <= 1e-6 * fmax(t, 1e-3)) break;      // at the offset time of impact
+      const double nt = t + step;
+      if (nt >= 1.0) {
+        t = 1.0;
+        break;
+      }
+      t = nt;
+    }
+    amin = fmin(amin, t);
   }
   amin = block_min<double, NT>(amin, 1.0);
   if (threadIdx.x == 0) partials[blockIdx.x] = amin;
@@ -623,6 +653,7 @@ bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool he
   A.sigma = S.sigma;
   A.grad = grad;
   A.hess = hess ? 1 : 0;
+  A.project = S.project ? 1 : 0;
   if (hess) {
     BAL_TRY(buf_reserve(S.emit_keys, sizeof(uint64_t) * 6 * S.n_eval));
     BAL_TRY(buf_reserve(S.emit_vals, sizeof(double) * 54 * S.n_eval));
@@ -652,7 +683,8 @@ bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
                              const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st) {
   constexpr int NT = 256;
   const int nblk = 2 * kNumSM;
-  k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound, S.partials);
+  k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound,
+                                        S.prm.ca_max_iter > 0 ? S.prm.ca_max_iter : 64, S.partials);
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);
 }

@@ -224,7 +224,7 @@ __device__ inline void add_block(double* dst, const double blk[3][3], bool trans
     for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, transpose ? blk[k][i] : blk[i][k]);
 }
 
-__global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __restrict__ x) {
+__global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __restrict__ x, int project) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S.nt; t += gridDim.x * blockDim.x) {
     int v[4];
     d3 X[4];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const double ev = A[k][k];
-        if (ev <= 0.0) continue;
+        if (project && ev <= 0.0) continue;
         // w[b][i] = sum_m U[i][m] q_m beta[b][m]
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
 #pragma unroll
       for (int sgn = 0; sgn < 2; ++sgn) {
         const double ev = sgn == 0 ? mu + q : mu - q;   // flip : twist
-        if (ev <= 0.0) continue;
+        if (project && ev <= 0.0) continue;
         const double sg = sgn == 0 ? 1.0 : -1.0;
         // D = U (E_ij +- E_ji) V^T / sqrt2 ; w[b] = (u_i beta_bj +- u_j beta_bi)/sqrt2
 #pragma unroll
@@ -346,6 +346,51 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
   }
 }
 
+// dJ/dE_e += -lambda_e^T (d grad W_e / d E_e) = -lambda_e^T grad W_e / E_e
+// (mu and lam are linear in E); pinned DOFs of lambda are zero.
+__global__ void k_dLdE(Dev S, const double* __restrict__ x, const double* __restrict__ lam_adj,
+                       const double* __restrict__ E, double* __restrict__ acc) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S.nt; t += gridDim.x * blockDim.x) {
+    int v[4];
+    d3 X[4];
+    load_tet(S, x, t, v, X);
+    const double* Mi = S.Dm_inv + 9 * (int64_t)t;
+    double F[3][3];
+    def_grad(X, Mi, F);
+    const double J = det3(F);
+    const double mu = S.mu[t], lam = S.lam[t], vol = S.vol[t];
+    const double lnJ = log(J);
+    double A[3][3];
+    A[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) / J;
+    A[0][1] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) / J;
+    A[0][2] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) / J;
+    A[1][0] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) / J;
+    A[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) / J;
+    A[1][2] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) / J;
+    A[2][0] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) / J;
+    A[2][1] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) / J;
+    A[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) / J;
+    double P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) P[i][j] = mu * (F[i][j] - A[i][j]) + lam * lnJ * A[i][j];
+    d3 gs = d3{0, 0, 0};
+    double dot_acc = 0.0;
+#pragma unroll
+    for (int b = 1; b < 4; ++b) {
+      const double* B = Mi + 3 * (b - 1);
+      d3 gb = d3{vol * (P[0][0] * B[0] + P[0][1] * B[1] + P[0][2] * B[2]),
+                 vol * (P[1][0] * B[0] + P[1][1] * B[1] + P[1][2] * B[2]),
+                 vol * (P[2][0] * B[0] + P[2][1] * B[1] + P[2][2] * B[2])};
+      gs = gs + gb;
+      dot_acc += dot(ld3(lam_adj, v[b]), gb);
+    }
+    dot_acc += dot(ld3(lam_adj, v[0]), -gs);
+    acc[t] -= dot_acc / E[t];
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_energy(Dev S, const double* __restrict__ x,
                                                double* __restrict__ partials, int nblk) {
@@ -402,9 +447,15 @@ bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st) {
   BAL_LAUNCH_CHECK();
   if (S.d.nnzL > 0) BAL_CUDA(cudaMemsetAsync(S.d.Lval, 0, sizeof(double) * 9 * S.d.nnzL, st));
   if (S.d.nt > 0) {
-    k_elastic_hess<<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x);
+    k_elastic_hess<<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, S.project ? 1 : 0);
     BAL_LAUNCH_CHECK();
   }
+  return BAL_OK;
+}
+
+bal_status launch_dLdE(Scene& S, const double* x, const double* lam_adj, double* acc, cudaStream_t st) {
+  k_dLdE<<<grid_for(S.d.nt), kThreads, 0, st>>>(S.d, x, lam_adj, S.E, acc);
+  BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
 

@@ -648,6 +648,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     info->refine_passes = passes;
     info->warm_iters = 0;
     info->n_groups = 0;
+    info->negative_curvature = 0;
   }
   return BAL_OK;
 }
@@ -700,6 +701,7 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
     info->refine_passes = 0;
     info->warm_iters = witers;
     info->n_groups = ngroups;
+    info->negative_curvature = 0;
     double rn, bn;
     BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
     info->rel_residual = bn > 0 ? rn / bn : rn;

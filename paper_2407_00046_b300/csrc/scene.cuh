@@ -80,6 +80,9 @@ struct Scene {
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
   bool f32_valid = false;
   bool assembled = false;
+  bool project = true;           // PSD projection of stencil Hessians (false: adjoint)
+  double* E = nullptr;           // [nt] Young's modulus (device)
+  std::vector<double> E_h, nu_h;
 
   // contact emission + sort scratch
   Buf emit_keys, emit_keys_alt, emit_idx, emit_idx_alt, emit_vals, seg_head, seg_pos;
@@ -132,6 +135,8 @@ bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st);
 // partial sums of (inertia, elastic) energy and an inversion count; result in
 // S.scal[0] (inertia), S.scal[1] (elastic), S.scal[2] (number of tets with J <= 0).
 bal_status launch_elastic_energy(Scene& S, const double* x, cudaStream_t st);
+// acc[e] += -lam_e^T grad W_e / E_e
+bal_status launch_dLdE(Scene& S, const double* x, const double* lam_adj, double* acc, cudaStream_t st);
 
 // ---- contact.cu ---------------------------------------------------------------
 // distances of n pairs (keys) at x into d (device).

@@ -58,3 +58,32 @@ def test_invariants_after_each_step():
         assert np.all(x[sc.pinned == 1] == xo[sc.pinned == 1])             # Dirichlet
         for r in info["log"]:
             assert r.get("alpha", 1.0) > 0
+
+
+def _pt_scene():
+    # one vertex (tiny tet) above a large triangle face (flat slab)
+    Xs, Ts = scenes.lattice_box(1, 1, 1, (0.2, 0.05, 0.2))
+    Xp, Tp = scenes.lattice_box(1, 1, 1, (0.01, 0.01, 0.01))
+    Xp = Xp + np.array([0.07, 0.05 + 0.004, 0.06])
+    return scenes.merge_bodies("pt", [dict(X=Xs, tets=Ts, E=1e5), dict(X=Xp, tets=Tp, E=1e5)])
+
+
+def test_step_bound_head_on_closed_form():
+    sc = _pt_scene()
+    m = system.make_model(sc)
+    p = np.zeros_like(sc.X)
+    p[sc.body == 1] = [0.0, -0.02, 0.0]        # closes 2 cm per unit step at a 4 mm gap
+    cand = contact.candidate_pairs(sc.X, sc, 0.05)
+    alpha = bal.step_bound(m, sc.X, p, cand, bal.Params())
+    assert alpha == pytest.approx(0.9 * 0.004 / 0.02, rel=1e-9)
+
+
+def test_step_bound_sliding_is_not_limited():
+    sc = _pt_scene()
+    m = system.make_model(sc)
+    p = np.zeros_like(sc.X)
+    p[sc.body == 1] = [0.03, 0.0, 0.02]          # tangential motion over the face
+    cand = contact.candidate_pairs(sc.X, sc, 0.05)
+    assert bal.step_bound(m, sc.X, p, cand, bal.Params()) == 1.0
+    p[sc.body == 1] = [0.03, -0.002, 0.02]       # mostly sliding, slowly closing: not limited either
+    assert bal.step_bound(m, sc.X, p, cand, bal.Params()) == 1.0
