@@ -101,6 +101,43 @@ def spmv_bytes(nv, nnzL, nnzC, p=8):
     return (nv + nnzL + nnzC) * 9 * p + (nnzL + nnzC) * 4 + (nv + 1) * 4 + 2 * 3 * nv * p
 
 
+def run_pcg_only(args):
+    """Assemble the Hessian of the workload once (at x_0 + one gravity step, the
+    free-fall iterate) and run a fixed number of PCG iterations on it: the
+    SpMV / PCG kernels in isolation (used for profiling)."""
+    import torch
+    from paper_2407_00046_b300 import bal, build, scenes
+    build.build(force=False, verbose=False)
+    dev = torch.device("cuda", 0)
+    sc = scenes.scene_by_name(args.scene)
+    params = bal.default_params(pcg_stall_window=1 << 30,
+                                precision=bal.PREC_MIXED if args.precision == "mixed" else bal.PREC_FP64,
+                                mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0)
+    S = bal.Scene(sc, params, pair_capacity=1 << 22)
+    x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
+    v = torch.tensor(sc.V0, dtype=torch.float64, device=dev)
+    S.step_begin(x, v)
+    g = torch.empty_like(x)
+    view = S.assemble_hessian(x, g)
+    b = -g
+    sol = torch.zeros_like(b)
+    S.pcg_solve(b, sol, 0.0, 20)
+    times = []
+    for _ in range(max(args.steps, 1)):
+        sol.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = S.pcg_solve(b, sol, 0.0, args.pcg_iters)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / max(info["iters"], 1))
+    ms = statistics.median(times)
+    return {"mode": "pcg", "scene": args.scene, "precision": args.precision,
+            "iters_per_solve": args.pcg_iters, "ms_per_iter": round(ms, 4),
+            "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "n_verts": sc.n_verts}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2407_00046_b300 import bal, build, scenes
@@ -110,7 +147,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     sc = scenes.scene_by_name(args.scene)
     params = bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
-                                newton_max_iter=args.newton_max,
+                                newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
+                                pcg_max_iter=30000,
                                 precision=bal.PREC_MIXED if args.precision == "mixed" else bal.PREC_FP64)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
@@ -229,7 +267,7 @@ def run_ours(args, rank, world):
         "config": {
             "workload": f"{sc.name}: {sc.n_tets} tets, {sc.n_verts} verts, h=1/30 s, dhat=1e-3 m",
             "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
-            "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol,
+            "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol, "pcg_stall_window": args.pcg_stall,
             "precond": "block-Jacobi", "precision": args.precision,
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
@@ -338,10 +376,19 @@ def main():
     ap.add_argument("--newton-tol", type=float, default=1e-4)
     ap.add_argument("--newton-max", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pcg-stall", type=int, default=5000,
+                    help="PCG stagnation window (App. B uses 100; see DESIGN.md)")
+    ap.add_argument("--mode", default="step", choices=["step", "pcg"],
+                    help="pcg: assemble once and time fixed-length PCG solves (profiling)")
+    ap.add_argument("--pcg-iters", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.mode == "pcg":
+        if rank == 0:
+            print(json.dumps(run_pcg_only(args)), flush=True)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)

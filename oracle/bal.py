@@ -17,9 +17,10 @@ paper used here (each one is recorded in the design notes):
   new iterate before mu_i += sigma b(d_i, dhat + s_i);
 * sigma update: sigma <- min(1.2 sigma, 100 sigma0) (the printed max(...) is
   read as a cap; the literal form is available as `sigma_literal_max`);
-* sigma0 = -(sum grad b)^T grad E / ||sum grad b||^2 over A at x_0 (the
-  printed denominator is not squared, which is not dimensionally
-  consistent), floored at mbar / (h^2 b''(dhat/2, dhat));
+* sigma0 = -(sum grad b)^T grad E / ||sum grad b||^2 over A (the printed
+  denominator is not squared, which is not dimensionally consistent), floored
+  at mbar / (h^2 b''(dhat/2, dhat)); evaluated at x_0, or, when A(x_0) is empty,
+  at the first iterate where A becomes non-empty;
 * line search: alpha_0 = the largest t <= 1 along x + t p over which every pair
   keeps 10% of its current distance, found per pair by conservative
   advancement with Delta_i = max |p_a - p_b| over a node of each primitive as
@@ -214,6 +215,9 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
         sigma0, Ap = frozen[0], dict(frozen[1])
     else:
         sigma0, Ap = initial_sigma(model, x, y, A_keys), {}
+    # the formula needs A != empty: when the step starts contact-free, sigma0 is
+    # taken at the first iterate where A becomes non-empty
+    sigma0_pending = frozen is None and not A_keys
     sigma = sigma0
     dmin_prev = math.inf
     info = dict(sigma0=sigma0, iters=0, converged=False, ls_failed=False, log=[])
@@ -222,6 +226,11 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
         if l > 0:
             A_keys, A_d = active_pairs(model, x)
         dmin = float(A_d.min()) if A_d.size else math.inf
+        if sigma0_pending and A_keys:
+            sigma0 = initial_sigma(model, x, y, A_keys)
+            sigma = sigma0
+            sigma0_pending = False
+            info["sigma0"] = sigma0
         if l > 0 and frozen is None:
             # dual update of the previous iteration, evaluated at x^[l]
             if Ap:

@@ -292,6 +292,14 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   BAL_TRY(detect_active(S, x, A, Ad, st));
   double dmin = INFINITY;
   for (double d : Ad) dmin = std::min(dmin, d);
+  if (S.sigma0_pending && !A.empty()) {
+    // sigma0 (Sec. 3.4) needs A != empty: taken at the first iterate with contact
+    double s0 = 0.0;
+    BAL_TRY(initial_sigma(S, x, A, &s0, st));
+    S.sigma0 = s0;
+    S.sigma = s0;
+    S.sigma0_pending = false;
+  }
   if (S.l > 0 && !S.prm.freeze_al) {
     // dual update of the previous iteration, evaluated at x^[l] (Alg. 1 lines 12-15)
     if (!S.ap_keys.empty()) {
@@ -806,6 +814,7 @@ bal_status bal_step_begin(bal_scene* sc, const double* x_t, const double* v_t, v
   S.l = 0;
   S.e0 = 0.0;
   S.step_active = true;
+  S.sigma0_pending = false;
   if (S.prm.freeze_al) return BAL_OK;   // keep sigma, A', mu as set by bal_set_al_state
   S.ap_keys.clear();
   S.ap_mu.clear();
@@ -817,6 +826,7 @@ bal_status bal_step_begin(bal_scene* sc, const double* x_t, const double* v_t, v
   BAL_TRY(initial_sigma(S, x_t, A, &s0, st));
   S.sigma0 = s0;
   S.sigma = s0;
+  S.sigma0_pending = A.empty();
   return BAL_OK;
 }
 
@@ -848,6 +858,7 @@ bal_status bal_set_al_state(bal_scene* sc, const bal_al_state* in) {
   Scene& S = sc->S;
   S.sigma = in->sigma;
   S.sigma0 = in->sigma0;
+  S.sigma0_pending = false;
   S.dmin_prev = in->dmin_prev;
   S.ap_keys.assign(in->ap_keys, in->ap_keys + in->n_ap);
   S.ap_mu.assign(in->ap_mu, in->ap_mu + in->n_ap);
@@ -1085,6 +1096,7 @@ bal_status bal_time_step(bal_scene* sc, double* x, double* v, bal_step_info* inf
     I.newton_iters += 1;
   }
   I.sigma_final = S.sigma;
+  I.sigma0 = S.sigma0;
   // v = (x - x_t) / h (Sec. 3.1)
   const int64_t n3 = 3 * (int64_t)S.d.nv;
   k_velocity<<<grid_for(n3), kThreads, 0, st>>>(n3, 1.0 / S.d.h, x, S.xt, v);

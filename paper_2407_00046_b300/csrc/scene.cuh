@@ -117,6 +117,7 @@ struct Scene {
   // AL state of the current time step (host copy is authoritative)
   bool step_active = false;
   double sigma = 0, sigma0 = 0, dmin_prev = 0, e0 = 0;
+  bool sigma0_pending = false;   // A(x_0) empty: sigma0 taken when contact appears
   int32_t l = 0;
   std::vector<uint64_t> ap_keys;
   std::vector<double> ap_mu;

@@ -1,0 +1,97 @@
+"""Parity at full workload sizes (663,552-tet cube stack, 1.77M-tet chain net):
+sampled vertex rows of the assembled Hessian and of the gradient against the
+oracle evaluated on the incident tets only, plus properties that hold at any
+size (SpMV symmetry, PCG residual)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import elastic  # noqa: E402
+from paper_2407_00046_b300 import bal, scenes  # noqa: E402
+
+DEV = "cuda"
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _oracle_rows(sc, x, verts, mass, project=True):
+    """Blocks H[v, u] (3x3) and gradients g[v] from the elastic stencils of the
+    tets incident to each sampled vertex plus the mass term (no contact)."""
+    Dm_inv, vol = elastic.rest_data(sc.X, sc.tets)
+    mu, lam = elastic.lame(sc.E, sc.nu)
+    h = sc.h
+    rows, grads = {}, {}
+    for v in verts:
+        tt = np.flatnonzero(np.any(sc.tets == v, axis=1))
+        _, g, H = elastic.element_terms(x, sc.tets[tt], Dm_inv[tt], vol[tt], mu[tt], lam[tt], project)
+        blocks = {v: np.eye(3) * mass[v] / h ** 2}
+        gv = np.zeros(3)
+        for k, t in enumerate(tt):
+            a = int(np.flatnonzero(sc.tets[t] == v)[0])
+            gv += g[k, 3 * a:3 * a + 3]
+            for b in range(4):
+                u = int(sc.tets[t, b])
+                blocks[u] = blocks.get(u, np.zeros((3, 3))) + H[k, 3 * a:3 * a + 3, 3 * b:3 * b + 3]
+        rows[v], grads[v] = blocks, gv
+    return rows, grads
+
+
+def _gpu_rows(S, view, verts):
+    h = S.copy_hessian(view)
+    nv = S.nv
+    rp, col = S.static_pattern()
+    D = h["D"].cpu().numpy().reshape(nv, 3, 3)
+    L = h["L"].cpu().numpy().reshape(-1, 3, 3)
+    out = {}
+    for v in verts:
+        blocks = {v: D[v]}
+        for s in range(rp[v], rp[v + 1]):            # row v: blocks (v, col)
+            blocks[int(col[s])] = L[s]
+        for s in np.flatnonzero(col == v):            # column v: transposes of (row, v)
+            r = int(np.searchsorted(rp, s, side="right") - 1)
+            blocks[r] = L[s].T
+        out[v] = blocks
+    return out
+
+
+@pytest.mark.parametrize("name", ["cube_stack", "chain_net_shells"])
+def test_sampled_rows_at_full_size(name):
+    sc = scenes.scene_by_name(name)
+    rng = np.random.default_rng(9)
+    S = bal.Scene(sc, bal.default_params(), pair_capacity=1 << 22)
+    mass = S.mass()
+    # a deformed, contact-free iterate: small random displacement of free vertices
+    x = sc.X + 2e-5 * rng.normal(size=sc.X.shape) * (sc.pinned == 0)[:, None]
+    S.step_begin(T(sc.X), T(sc.V0))
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    view = S.assemble_hessian(T(x), g)
+    assert view["nnz_C"] == 0
+    free = np.flatnonzero(sc.pinned == 0)
+    verts = [int(v) for v in rng.choice(free, 24, replace=False)]
+    ro, go = _oracle_rows(sc, x, verts, mass)
+    rg = _gpu_rows(S, view, verts)
+    y = sc.X + sc.h * sc.V0 + sc.h ** 2 * sc.gravity[None, :]
+    gg = g.cpu().numpy().reshape(-1, 3)
+    for v in verts:
+        scale = max(np.abs(B).max() for B in ro[v].values())
+        for u, B in ro[v].items():
+            if sc.pinned[u]:
+                continue
+            assert np.abs(rg[v][u] - B).max() <= 1e-10 * scale, (v, u)
+        ref = go[v] + mass[v] * (x[v] - y[v]) / sc.h ** 2
+        assert np.abs(gg[v] - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-30)
+    # properties at full size: symmetric SpMV, PCG residual
+    u1 = torch.randn(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    u2 = torch.randn_like(u1)
+    h1, h2 = torch.empty_like(u1), torch.empty_like(u1)
+    S.spmv(u1, h1)
+    S.spmv(u2, h2)
+    a, b = float(u2 @ h1), float(u1 @ h2)
+    assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    sol = torch.zeros_like(u1)
+    info = S.pcg_solve(-g, sol, 1e-6, 1000)
+    assert info["iters"] > 0 and np.isfinite(info["rel_residual"])
