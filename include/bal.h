@@ -159,6 +159,8 @@ typedef struct {
   double pcg_rel_residual;
   double energy;              /* L_sigma at the accepted iterate */
   double ms_assemble, ms_solve, ms_line_search, ms_contact;
+  double ms_ls_broad, ms_ls_bound, ms_ls_energy;   /* line-search breakdown */
+  int64_t n_raw_candidates;   /* line-search pairs from the broad phase, before filtering */
 } bal_newton_info;
 
 typedef struct {

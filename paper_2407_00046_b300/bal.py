@@ -80,7 +80,9 @@ class NewtonInfo(C.Structure):
                 ("ls_trials", C.c_int32), ("pcg_iters", C.c_int32),
                 ("pcg_rel_residual", C.c_double), ("energy", C.c_double),
                 ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
-                ("ms_line_search", C.c_double), ("ms_contact", C.c_double)]
+                ("ms_line_search", C.c_double), ("ms_contact", C.c_double),
+                ("ms_ls_broad", C.c_double), ("ms_ls_bound", C.c_double),
+                ("ms_ls_energy", C.c_double), ("n_raw_candidates", C.c_int64)]
 
 
 class StepInfo(C.Structure):

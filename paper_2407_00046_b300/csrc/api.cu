@@ -377,7 +377,9 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   t0 = clk::now();
   bool extra_done = false;
   for (;;) {
+    auto tb = clk::now();
     BAL_TRY(find_candidates_motion(S, x, S.dir, S.ls_cand, S.ls_cand_alt, &S.n_ls_cand, st));
+    I.n_raw_candidates = S.n_ls_cand;
     if (S.n_ls_cand > 0) {   // keep the pairs that can enter A or bound alpha
       BAL_TRY(buf_reserve(S.flags, S.n_ls_cand));
       BAL_TRY(buf_reserve(S.ls_cand_alt, sizeof(uint64_t) * S.n_ls_cand));
@@ -390,6 +392,9 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
       S.n_ls_cand = nk;
     }
     I.n_candidates = S.n_ls_cand;
+    BAL_CUDA(cudaStreamSynchronize(st));
+    I.ms_ls_broad += ms_since(tb);
+    tb = clk::now();
     double alpha = 1.0;
     if (S.n_ls_cand > 0) {
       BAL_TRY(launch_step_bound(S, x, S.dir, S.ls_cand.as<uint64_t>(), S.n_ls_cand, 14, st));
@@ -397,6 +402,8 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
       BAL_TRY(read_scalars(S, &ab, 14, 1, st));
       alpha = std::min(1.0, ab);
     }
+    I.ms_ls_bound += ms_since(tb);
+    tb = clk::now();
     double P0[5];
     BAL_TRY(energy_parts(S, x, S.ls_cand.as<uint64_t>(), S.n_ls_cand, P0, st));
     const double E_old = P0[0] + P0[1] + P0[2];
@@ -421,6 +428,7 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
       alpha *= 0.5;
     }
     I.ls_trials += trials;
+    I.ms_ls_energy += ms_since(tb);
     if (ok) {
       I.alpha = alpha;
       BAL_CUDA(cudaMemcpyAsync(x, S.xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
