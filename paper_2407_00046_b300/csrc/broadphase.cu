@@ -20,7 +20,9 @@ namespace bal {
 
 namespace {
 
-constexpr int kOff = 1 << 20;
+// cell key: 16 bits per axis (bits 16..63) + 16 bits of body id (motion passes)
+constexpr int kOff = 1 << 15;
+constexpr uint32_t kBodySat = 0xffffu;   // body ids >= this share one id (no skipping)
 constexpr int64_t kMaxCellsPerPrim = 1 << 20;
 
 // Per-vertex inflation radius r_v; a primitive's radius is the max over its
@@ -49,6 +51,11 @@ __device__ inline double vert_r(const Grid& G, int v) {
   if (G.mode == 2) r += sqrt(dot(pb, pb));
   return r / G.eta + G.base;
 }
+__device__ inline uint32_t body_bits(const Grid& G, int v) {
+  if (G.mode == 0) return 0u;
+  const uint32_t b = (uint32_t)G.body[v];
+  return b < kBodySat ? b : kBodySat;
+}
 __device__ inline bool body_ok(const Grid& G, int va, int vb) {
   if (G.mode == 0) return true;
   return G.mode == 1 ? G.body[va] == G.body[vb] : G.body[va] != G.body[vb];
@@ -60,7 +67,7 @@ __device__ inline int cell_of(double v, double inv_c) {
   return (int)f;
 }
 __device__ inline uint64_t cell_key(int ix, int iy, int iz) {
-  return ((uint64_t)(ix + kOff) << 42) | ((uint64_t)(iy + kOff) << 21) | (uint64_t)(iz + kOff);
+  return ((uint64_t)(ix + kOff) << 48) | ((uint64_t)(iy + kOff) << 32) | ((uint64_t)(iz + kOff) << 16);
 }
 
 struct Box {
@@ -134,7 +141,7 @@ __global__ void k_fill_cells(Dev S, const double* __restrict__ x, int kind, int 
       for (int iy = y0; iy <= y1; ++iy)
         for (int iz = z0; iz <= z1; ++iz) {
           if (o >= end) return;
-          cells[o] = cell_key(ix, iy, iz);
+          cells[o] = cell_key(ix, iy, iz) | body_bits(G, v[0]);
           ids[o] = i;
           ++o;
         }
@@ -148,6 +155,22 @@ __device__ inline int64_t lower_bound(const uint64_t* a, int64_t n, uint64_t k) 
     if (a[mid] < k) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// entries of one cell a query of body bits qb has to look at: [a0,a1) and [b0,b1)
+__device__ inline void cell_ranges(const Grid& G, const uint64_t* cells, int64_t n, uint64_t base,
+                                   uint32_t qb, int64_t& a0, int64_t& a1, int64_t& b0, int64_t& b1) {
+  const int64_t lo = lower_bound(cells, n, base), hi = lower_bound(cells, n, base + 0x10000ull);
+  if (G.mode == 0 || qb == kBodySat) {
+    a0 = lo; a1 = hi; b0 = b1 = hi;
+    return;
+  }
+  const int64_t ml = lower_bound(cells, n, base | qb), mh = lower_bound(cells, n, (base | qb) + 1);
+  if (G.mode == 1) {        // same body only
+    a0 = ml; a1 = mh; b0 = b1 = mh;
+  } else {                  // other bodies only
+    a0 = lo; a1 = ml; b0 = mh; b1 = hi;
+  }
 }
 
 __device__ inline void emit(uint64_t* out, unsigned long long* counter, int64_t cap, uint64_t key) {
@@ -174,9 +197,12 @@ __global__ void k_pt_query(Dev S, const double* __restrict__ x, Grid G,
     for (int ix = x0; ix <= x1; ++ix)
       for (int iy = y0; iy <= y1; ++iy)
         for (int iz = z0; iz <= z1; ++iz) {
-          const uint64_t key = cell_key(ix, iy, iz);
-          for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
-            const int t = ids[k];
+          int64_t r0, r1, r2, r3;
+          cell_ranges(G, cells, ncell, cell_key(ix, iy, iz), body_bits(G, v), r0, r1, r2, r3);
+          for (int64_t kk = r0; kk < r3; ++kk) {
+            if (kk == r1) kk = r2;
+            if (kk >= r3) break;
+            const int t = ids[kk];
             int tv[3], nv;
             prim_verts(S, 0, t, tv, nv);
             if (tv[0] == v || tv[1] == v || tv[2] == v) continue;
@@ -202,9 +228,12 @@ __global__ void k_ee_query(Dev S, const double* __restrict__ x, Grid G,
     for (int ix = x0; ix <= x1; ++ix)
       for (int iy = y0; iy <= y1; ++iy)
         for (int iz = z0; iz <= z1; ++iz) {
-          const uint64_t key = cell_key(ix, iy, iz);
-          for (int64_t k = lower_bound(cells, ncell, key); k < ncell && cells[k] == key; ++k) {
-            const int f = ids[k];
+          int64_t r0, r1, r2, r3;
+          cell_ranges(G, cells, ncell, cell_key(ix, iy, iz), body_bits(G, ev[0]), r0, r1, r2, r3);
+          for (int64_t kk = r0; kk < r3; ++kk) {
+            if (kk == r1) kk = r2;
+            if (kk >= r3) break;
+            const int f = ids[kk];
             if (f <= e) continue;
             int fv[3];
             prim_verts(S, 1, f, fv, nv);
@@ -251,9 +280,9 @@ bal_status build_cells(Scene& S, const double* x, int kind, int n, Grid G, int64
   cub::DoubleBuffer<uint64_t> dk(S.bp_cells.as<uint64_t>(), S.bp_cells_alt.as<uint64_t>());
   cub::DoubleBuffer<int32_t> dv(S.bp_ids.as<int32_t>(), S.bp_ids_alt.as<int32_t>());
   tmp = 0;
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, (int64_t)total, 0, 63, st));
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, (int64_t)total, 0, 64, st));
   BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, (int64_t)total, 0, 63, st));
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, (int64_t)total, 0, 64, st));
   *ncell = total;
   *cells_out = dk.Current();
   *ids_out = dv.Current();
