@@ -709,6 +709,7 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dupload(S, (const int32_t**)&S.body, (const int32_t*)body.data(), body.size()));
   TRYC(dupload(S, (const double**)&S.body_inv_cnt, (const double*)bcnt.data(), bcnt.size()));
   TRYC(dalloc(S, &S.bmean, 3 * (size_t)S.nbody));
+  TRYC(dalloc(S, &S.bmot, (size_t)S.nbody));
   TRYC(dalloc(S, &S.d.D, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.d.Dinv, 9 * (size_t)nv));
   TRYC(dalloc(S, &S.d.Lval, 9 * (size_t)S.d.nnzL));
@@ -767,7 +768,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
                  &S.emit_idx_alt, &S.emit_vals, &S.seg_head, &S.seg_pos, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
-                 &S.ls_cand, &S.ls_cand_alt, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d};
+                 &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d};
   for (Buf* b : bufs) buf_free(*b);
   delete sc;
   return BAL_OK;

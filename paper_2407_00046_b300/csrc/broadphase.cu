@@ -13,6 +13,8 @@
 // primitive's cell range, never the grid.
 // (The paper's broad phase is an LBVH, Sec. 5.3; the grid is this build's.)
 #include <cub/cub.cuh>
+#include <cstring>
+#include <vector>
 
 #include "scene.cuh"
 
@@ -38,6 +40,7 @@ struct Grid {
   int mode;
   const double* dir;
   const double* bmean;   // [nbody][3]
+  const double* bmot;    // [nbody] half the largest mean relative motion to an interacting body
   const int32_t* body;   // [nv]
   double eta, base;
 };
@@ -48,7 +51,7 @@ __device__ inline double vert_r(const Grid& G, int v) {
   const d3 pb = d3{G.bmean[3 * b], G.bmean[3 * b + 1], G.bmean[3 * b + 2]};
   const d3 w = ld3(G.dir, v) - pb;
   double r = sqrt(dot(w, w));
-  if (G.mode == 2) r += sqrt(dot(pb, pb));
+  if (G.mode == 2) r += G.bmot[b];
   return r / G.eta + G.base;
 }
 __device__ inline uint32_t body_bits(const Grid& G, int v) {
@@ -294,6 +297,36 @@ __global__ void k_body_mean(Dev S, const int32_t* __restrict__ body, const doubl
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x)
     atomic_add3(bsum, body[v], ld3(dir, v));
 }
+// order-preserving 64-bit image of a double (for atomic min / max)
+__device__ inline unsigned long long ord(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+// per body: max |p_v - pbar_B| and the AABB of its vertices at x
+__global__ void k_body_stats(Dev S, const int32_t* __restrict__ body, const double* __restrict__ x,
+                             const double* __restrict__ dir, const double* __restrict__ bmean,
+                             unsigned long long* __restrict__ stats) {   // [nb][7]
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x) {
+    const int b = body[v];
+    const d3 w = ld3(dir, v) - d3{bmean[3 * b], bmean[3 * b + 1], bmean[3 * b + 2]};
+    unsigned long long* st = stats + 7 * (int64_t)b;
+    atomicMax(st, ord(sqrt(dot(w, w))));
+    const d3 p = ld3(x, v);
+    atomicMin(st + 1, ord(p.x));
+    atomicMin(st + 2, ord(p.y));
+    atomicMin(st + 3, ord(p.z));
+    atomicMax(st + 4, ord(p.x));
+    atomicMax(st + 5, ord(p.y));
+    atomicMax(st + 6, ord(p.z));
+  }
+}
+__global__ void k_stats_init(unsigned long long* stats, int nb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 7 * nb; i += gridDim.x * blockDim.x) {
+    const int k = i % 7;
+    stats[i] = (k >= 1 && k <= 3) ? ~0ull : 0ull;
+  }
+}
+
 __global__ void k_body_div(double* bsum, const double* __restrict__ inv_cnt, int nb) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
     bsum[3 * b] *= inv_cnt[b];
@@ -379,23 +412,77 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
   return collect(S, x, &G, 1, out, alt, n, st);
 }
 
+static inline double unord(unsigned long long u) {
+  const unsigned long long v = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+  double d;
+  std::memcpy(&d, &v, sizeof(d));
+  return d;
+}
+
 bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, Buf& out, Buf& alt,
                                   int64_t* n, cudaStream_t st) {
-  // per-body mean displacement of the step
-  BAL_CUDA(cudaMemsetAsync(S.bmean, 0, sizeof(double) * 3 * S.nbody, st));
+  const int nb = S.nbody;
+  // per-body mean displacement of the step, deviation bound and AABB
+  BAL_CUDA(cudaMemsetAsync(S.bmean, 0, sizeof(double) * 3 * nb, st));
   k_body_mean<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.body, dir, S.bmean);
   BAL_LAUNCH_CHECK();
-  k_body_div<<<grid_for(S.nbody), kThreads, 0, st>>>(S.bmean, S.body_inv_cnt, S.nbody);
+  k_body_div<<<grid_for(nb), kThreads, 0, st>>>(S.bmean, S.body_inv_cnt, nb);
   BAL_LAUNCH_CHECK();
+  BAL_TRY(buf_reserve(S.bstats, sizeof(unsigned long long) * 7 * nb));
+  unsigned long long* stats = S.bstats.as<unsigned long long>();
+  k_stats_init<<<grid_for(7 * nb), kThreads, 0, st>>>(stats, nb);
+  k_body_stats<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.body, x, dir, S.bmean, stats);
+  BAL_LAUNCH_CHECK();
+  std::vector<double> pm(3 * nb);
+  std::vector<unsigned long long> sh(7 * (size_t)nb);
+  BAL_CUDA(cudaMemcpyAsync(pm.data(), S.bmean, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaMemcpyAsync(sh.data(), stats, sizeof(unsigned long long) * 7 * nb, cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  // Bodies B, C can hold a pair with d < Delta/eta + dhat only if their boxes
+  // are within (rho_B + rho_C + |pbar_B - pbar_C|)/eta + dhat; each body is then
+  // inflated by half of the largest |pbar_B - pbar_C| over such C.
+  const double eta = S.prm.step_bound, dh = S.d.dhat;
+  std::vector<double> mot(nb, 0.0);
+  if (nb <= 8192) {
+    for (int b = 0; b < nb; ++b) {
+      const unsigned long long* sb = &sh[7 * (size_t)b];
+      for (int c = b + 1; c < nb; ++c) {
+        const unsigned long long* sc = &sh[7 * (size_t)c];
+        const double dx = pm[3 * b] - pm[3 * c], dy = pm[3 * b + 1] - pm[3 * c + 1],
+                     dz = pm[3 * b + 2] - pm[3 * c + 2];
+        const double m = std::sqrt(dx * dx + dy * dy + dz * dz);
+        const double reach = (unord(sb[0]) + unord(sc[0]) + m) / eta + dh;
+        double gap2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          const double g = std::max(unord(sc[1 + k]) - unord(sb[4 + k]), unord(sb[1 + k]) - unord(sc[4 + k]));
+          if (g > 0) gap2 += g * g;
+        }
+        if (gap2 > reach * reach) continue;
+        mot[b] = std::max(mot[b], 0.5 * m);
+        mot[c] = std::max(mot[c], 0.5 * m);
+      }
+    }
+  } else {   // many bodies: |pbar_B - pbar_C| <= |pbar_B - q| + |pbar_C - q|, q = mean
+    double q[3] = {0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+      for (int k = 0; k < 3; ++k) q[k] += pm[3 * b + k] / nb;
+    for (int b = 0; b < nb; ++b) {
+      double s2 = 0;
+      for (int k = 0; k < 3; ++k) s2 += (pm[3 * b + k] - q[k]) * (pm[3 * b + k] - q[k]);
+      mot[b] = std::sqrt(s2);
+    }
+  }
+  BAL_CUDA(cudaMemcpyAsync(S.bmot, mot.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
   Grid P[2];
   for (int k = 0; k < 2; ++k) {
     P[k] = Grid{};
     P[k].mode = 1 + k;
     P[k].dir = dir;
     P[k].bmean = S.bmean;
+    P[k].bmot = S.bmot;
     P[k].body = S.body;
-    P[k].eta = S.prm.step_bound;
-    P[k].base = 0.5 * S.d.dhat;
+    P[k].eta = eta;
+    P[k].base = 0.5 * dh;
     constexpr int NT = 256;
     k_rsum<NT><<<2 * kNumSM, NT, 0, st>>>(S.d, P[k], S.partials);
     BAL_LAUNCH_CHECK();
@@ -405,9 +492,9 @@ bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, 
   BAL_CUDA(cudaMemcpyAsync(rm, S.scal + 15, sizeof(rm), cudaMemcpyDeviceToHost, st));
   BAL_CUDA(cudaStreamSynchronize(st));
   // rmax holds the mean surface radius: it only sets the cell size
-  P[0].rmax = S.d.nsv ? rm[0] / S.d.nsv : S.d.dhat;
-  P[1].rmax = S.d.nsv ? rm[1] / S.d.nsv : S.d.dhat;
-  const int npass = S.nbody > 1 ? 2 : 1;
+  P[0].rmax = S.d.nsv ? rm[0] / S.d.nsv : dh;
+  P[1].rmax = S.d.nsv ? rm[1] / S.d.nsv : dh;
+  const int npass = nb > 1 ? 2 : 1;
   return collect(S, x, P, npass, out, alt, n, st);
 }
 

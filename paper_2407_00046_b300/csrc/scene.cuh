@@ -109,6 +109,8 @@ struct Scene {
   int32_t* body = nullptr;        // [nv]
   double* body_inv_cnt = nullptr; // [nbody]
   double* bmean = nullptr;        // [nbody][3]
+  double* bmot = nullptr;         // [nbody] motion inflation of the inter-body pass
+  Buf bstats;                     // per-body deviation bound + AABB (ordered bits)
   // reductions
   double* partials = nullptr;    // [kMaxPartials]
   double* scal = nullptr;        // [64] scalar results
