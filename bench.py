@@ -273,6 +273,9 @@ def run_ours(args, rank, world):
             "parallelism": f"replicas x{world}",
         },
         "newton_iters_per_step": newton / max(args.steps, 1),
+        "newton_cap": args.newton_max,
+        "steps_converged": sum(int(t["converged"]) for t in timed),
+        "ms_per_newton_iter": round(ms / max(newton, 1), 2),
         "pcg_iters_per_step": pcg_iters / max(args.steps, 1) / max(world, 1),
         "pcg_only_iters_per_s": round(pcg_only, 1),
         "max_active_pairs": max((t["max_active"] for t in timed), default=0),
@@ -367,14 +370,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scene", default="chain_net_shells")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
-    ap.add_argument("--newton-max", type=int, default=60)
+    ap.add_argument("--newton-max", type=int, default=20,
+                    help="Newton iterations per time step (cap; the step reports convergence)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-stall", type=int, default=5000,
                     help="PCG stagnation window (App. B uses 100; see DESIGN.md)")
