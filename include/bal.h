@@ -175,6 +175,9 @@ typedef struct {
 
 /* ---- lifetime ------------------------------------------------------------ */
 BAL_API const char* bal_last_error(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (its own kernels; library sort / scan kernels are not counted). */
+BAL_API uint64_t bal_launch_count(void);
 BAL_API void bal_default_params(bal_params* out);
 
 /* Copies the topology, precomputes D_m^{-1}, rest volumes, Lame parameters and

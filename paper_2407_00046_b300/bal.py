@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib = C.CDLL(path)
     sigs = {
         "bal_last_error": ([], C.c_char_p),
+        "bal_launch_count": ([], C.c_uint64),
         "bal_default_params": ([C.POINTER(Params)], None),
         "bal_create_scene": ([C.POINTER(SceneDesc), C.POINTER(Params), C.POINTER(P)], C.c_int),
         "bal_destroy_scene": ([P], C.c_int),
@@ -147,6 +148,11 @@ def load(path: str = LIB_PATH):
 def _check(status):
     if status != OK:
         raise BalError(status, load().bal_last_error().decode())
+
+
+def launch_count() -> int:
+    """Kernels launched by libbal in this process so far."""
+    return int(load().bal_launch_count())
 
 
 def default_params(**kw) -> Params:

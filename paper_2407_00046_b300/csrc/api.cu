@@ -4,6 +4,7 @@
 // discrete decisions (A' rule, sigma schedule, convergence, line-search
 // acceptance) from scalars the kernels reduce on the device; every array
 // operation runs in the CUDA kernels of this library.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -22,6 +23,9 @@ namespace bal {
 
 // ---- errors --------------------------------------------------------------------
 static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -492,6 +496,8 @@ using namespace bal;
 extern "C" {
 
 const char* bal_last_error(void) { return g_err; }
+
+uint64_t bal_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void bal_default_params(bal_params* p) {
   if (!p) return;
@@ -1041,6 +1047,7 @@ bal_status bal_adjoint_step(bal_scene* sc, const double* x_t, const double* v_t,
   BAL_TRY(build_eval(S, x_next, A, st));
   const int64_t n3 = 3 * (int64_t)S.d.nv;
   k_adj_rhs<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, gx, gv, S.gtmp);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   bal_solve_info si;
   std::memset(&si, 0, sizeof(si));
@@ -1063,6 +1070,7 @@ bal_status bal_adjoint_step(bal_scene* sc, const double* x_t, const double* v_t,
   S.prm.precision = keep_prec;
   BAL_TRY(s);
   k_adj_out<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.dir, gv, dx, dv);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(launch_dLdE(S, x_next, S.dir, dE, st));
   BAL_CUDA(cudaStreamSynchronize(st));
@@ -1109,6 +1117,7 @@ bal_status bal_time_step(bal_scene* sc, double* x, double* v, bal_step_info* inf
   // v = (x - x_t) / h (Sec. 3.1)
   const int64_t n3 = 3 * (int64_t)S.d.nv;
   k_velocity<<<grid_for(n3), kThreads, 0, st>>>(n3, 1.0 / S.d.h, x, S.xt, v);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_CUDA(cudaStreamSynchronize(st));
   I.ms_total = ms_since(t0);

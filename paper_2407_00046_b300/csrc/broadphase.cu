@@ -260,6 +260,7 @@ bal_status build_cells(Scene& S, const double* x, int kind, int n, Grid G, int64
   int64_t* cnt = S.bp_count.as<int64_t>();
   int64_t* offs = S.bp_offs.as<int64_t>();
   k_count_cells<<<grid_for(n), kThreads, 0, st>>>(S.d, x, kind, n, G, cnt);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_CUDA(cudaMemsetAsync(cnt + n, 0, sizeof(int64_t), st));
   size_t tmp = 0;
@@ -279,6 +280,7 @@ bal_status build_cells(Scene& S, const double* x, int kind, int n, Grid G, int64
   BAL_TRY(buf_reserve(S.bp_ids_alt, sizeof(int32_t) * total));
   k_fill_cells<<<grid_for(n), kThreads, 0, st>>>(S.d, x, kind, n, G, offs,
                                                  S.bp_cells.as<uint64_t>(), S.bp_ids.as<int32_t>());
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   cub::DoubleBuffer<uint64_t> dk(S.bp_cells.as<uint64_t>(), S.bp_cells_alt.as<uint64_t>());
   cub::DoubleBuffer<int32_t> dv(S.bp_ids.as<int32_t>(), S.bp_ids_alt.as<int32_t>());
@@ -353,12 +355,14 @@ bal_status grid_pass(Scene& S, const double* x, Grid& G, Buf& out, int64_t cap,
   if (ncell > 0 && S.d.nsv > 0) {
     k_pt_query<<<grid_for(S.d.nsv), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
                                                         out.as<uint64_t>(), counter, cap);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }
   BAL_TRY(build_cells(S, x, 1, S.d.ne, G, &ncell, &cells, &ids, st));
   if (ncell > 0) {
     k_ee_query<<<grid_for(S.d.ne), kThreads, 0, st>>>(S.d, x, G, cells, ids, ncell,
                                                        out.as<uint64_t>(), counter, cap);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }
   return BAL_OK;
@@ -425,13 +429,17 @@ bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, 
   // per-body mean displacement of the step, deviation bound and AABB
   BAL_CUDA(cudaMemsetAsync(S.bmean, 0, sizeof(double) * 3 * nb, st));
   k_body_mean<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.body, dir, S.bmean);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   k_body_div<<<grid_for(nb), kThreads, 0, st>>>(S.bmean, S.body_inv_cnt, nb);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(buf_reserve(S.bstats, sizeof(unsigned long long) * 7 * nb));
   unsigned long long* stats = S.bstats.as<unsigned long long>();
   k_stats_init<<<grid_for(7 * nb), kThreads, 0, st>>>(stats, nb);
+  ::bal::note_launch();
   k_body_stats<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, S.body, x, dir, S.bmean, stats);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   std::vector<double> pm(3 * nb);
   std::vector<unsigned long long> sh(7 * (size_t)nb);
@@ -485,6 +493,7 @@ bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, 
     P[k].base = 0.5 * dh;
     constexpr int NT = 256;
     k_rsum<NT><<<2 * kNumSM, NT, 0, st>>>(S.d, P[k], S.partials);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
     BAL_TRY(finish_reduce(S, 2 * kNumSM, 15 + k, RED_SUM, st));
   }

@@ -11,6 +11,7 @@ namespace bal {
 
 // ---- host error plumbing ---------------------------------------------------
 void set_error(const char* fmt, ...);
+void note_launch(int n = 1);   // counts this library's kernel launches (bal_launch_count)
 bal_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 #define BAL_CUDA(call)                                                               \

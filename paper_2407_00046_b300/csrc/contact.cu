@@ -637,6 +637,7 @@ bal_status launch_pair_distance(Scene& S, const double* x, const uint64_t* keys,
                                 double* d, cudaStream_t st) {
   if (n <= 0) return BAL_OK;
   k_pair_distance<<<grid_for(n), kThreads, 0, st>>>(S.d, x, keys, n, d);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -661,6 +662,7 @@ bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool he
   A.emit_keys = S.emit_keys.as<uint64_t>();
   A.emit_vals = S.emit_vals.as<double>();
   k_contact_terms<<<grid_for(S.n_eval, 128, kNumSM * 8), 128, 0, st>>>(S.d, x, A);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -673,6 +675,7 @@ bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand
   k_contact_energy<NT><<<nblk, NT, 0, st>>>(S.d, x, cand, ncand, S.ap_keys_d.as<uint64_t>(),
                                             S.ap_mu_d.as<double>(), S.ap_s_d.as<double>(), nap,
                                             S.sigma, S.partials, nblk);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(finish_reduce_offset(S, 0, nblk, slot, RED_SUM, st));
   BAL_TRY(finish_reduce_offset(S, nblk, nblk, slot + 1, RED_SUM, st));
@@ -685,6 +688,7 @@ bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
   const int nblk = 2 * kNumSM;
   k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound,
                                         S.prm.ca_max_iter > 0 ? S.prm.ca_max_iter : 64, S.partials);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);
 }
@@ -693,6 +697,7 @@ bal_status launch_ls_filter(Scene& S, const double* x, const double* dir, const 
                             int64_t n, uint8_t* flag, cudaStream_t st) {
   if (n <= 0) return BAL_OK;
   k_ls_filter<<<grid_for(n), kThreads, 0, st>>>(S.d, x, dir, cand, n, S.prm.step_bound, flag);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -700,6 +705,7 @@ bal_status launch_ls_filter(Scene& S, const double* x, const double* dir, const 
 bal_status launch_flag_below(const double* d, int64_t n, double thr, uint8_t* flag, cudaStream_t st) {
   if (n <= 0) return BAL_OK;
   k_flag_below<<<grid_for(n), kThreads, 0, st>>>(d, n, thr, flag);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -708,6 +714,7 @@ bal_status launch_dual_update(Scene& S, const double* x, int64_t n, cudaStream_t
   if (n <= 0) return BAL_OK;
   k_dual_update<<<grid_for(n), kThreads, 0, st>>>(S.d, x, S.ap_keys_d.as<uint64_t>(),
                                                  S.ap_mu_d.as<double>(), n, S.sigma);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }

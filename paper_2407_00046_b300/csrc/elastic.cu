@@ -436,18 +436,22 @@ __global__ void __launch_bounds__(NT) k_energy(Dev S, const double* __restrict__
 
 bal_status launch_inertia_elastic_grad(Scene& S, const double* x, double* grad, cudaStream_t st) {
   k_inertia_grad<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, x, grad);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   k_elastic_grad<<<grid_for(S.d.nt), kThreads, 0, st>>>(S.d, x, grad);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
 
 bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st) {
   k_assemble_init<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   if (S.d.nnzL > 0) BAL_CUDA(cudaMemsetAsync(S.d.Lval, 0, sizeof(double) * 9 * S.d.nnzL, st));
   if (S.d.nt > 0) {
     k_elastic_hess<<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, S.project ? 1 : 0);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }
   return BAL_OK;
@@ -455,6 +459,7 @@ bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st) {
 
 bal_status launch_dLdE(Scene& S, const double* x, const double* lam_adj, double* acc, cudaStream_t st) {
   k_dLdE<<<grid_for(S.d.nt), kThreads, 0, st>>>(S.d, x, lam_adj, S.E, acc);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -463,6 +468,7 @@ bal_status launch_elastic_energy(Scene& S, const double* x, cudaStream_t st) {
   constexpr int NT = 256;
   const int nblk = 2 * kNumSM;
   k_energy<NT><<<nblk, NT, 0, st>>>(S.d, x, S.partials, nblk);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(finish_reduce(S, nblk, 0, RED_SUM, st));
   BAL_TRY(finish_reduce_offset(S, nblk, nblk, 1, RED_SUM, st));

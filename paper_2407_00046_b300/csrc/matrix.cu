@@ -28,7 +28,7 @@ namespace bal {
 
 namespace {
 
-constexpr int kRedBlocks = 2 * kNumSM;   // CTAs of every fused reduction kernel
+constexpr int kRedBlocks = 8 * kNumSM;   // CTAs of every fused PCG reduction kernel (latency hiding)
 constexpr int kRedThreads = 256;
 
 template <int NT>
@@ -423,9 +423,11 @@ Sys<float> sys32(Scene& S) {
 template <typename T>
 bal_status spmv_t(const Sys<T>& A, const T* v, T* y, cudaStream_t st) {
   k_spmv_diag<T><<<grid_for(A.nv), kThreads, 0, st>>>(A, v, y);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   if (A.O.nL + A.O.nC > 0) {
     k_spmv_offdiag<T><<<grid_for(A.O.nL + A.O.nC, kThreads, kNumSM * 16), kThreads, 0, st>>>(A.O, v, y);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }
   return BAL_OK;
@@ -442,6 +444,7 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
   init.window = window > 0 ? window : (1 << 30);
   BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   k_pcg_init<T, NT><<<G, NT, 0, st>>>(A, b, y0, r, z, S.pcg, S.partials, tol);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   PcgScalars h{};
   const int chunk = 16;
@@ -453,8 +456,11 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
     const int n = std::min(chunk, max_it - launched);
     for (int k = 0; k < n; ++k) {
       k_pcg_dir_diag<T, NT><<<G, NT, 0, st>>>(A, z, p, q, S.pcg, S.partials);
+      ::bal::note_launch();
       k_pcg_offdiag<T, NT><<<G, NT, 0, st>>>(A.O, p, q, S.pcg, S.partials, G);
+      ::bal::note_launch();
       k_pcg_update<T, NT><<<G, NT, 0, st>>>(A, x, p, q, r, z, S.pcg, S.partials);
+      ::bal::note_launch();
     }
     BAL_LAUNCH_CHECK();
     launched += n;
@@ -471,6 +477,7 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
 
 bal_status finish_reduce_offset(Scene& S, int offset, int n, int slot, RedOp op, cudaStream_t st) {
   k_finish<256><<<1, 256, 0, st>>>(S.partials + offset, n, S.scal + slot, (int)op);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -484,6 +491,7 @@ bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
   BAL_TRY(buf_reserve(S.seg_head, sizeof(int32_t) * (n_emit + 1)));
   BAL_TRY(buf_reserve(S.seg_pos, sizeof(int32_t) * (n_emit + 1)));
   k_iota<<<grid_for(n_emit), kThreads, 0, st>>>(S.emit_idx.as<int32_t>(), n_emit);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   cub::DoubleBuffer<uint64_t> dk(S.emit_keys.as<uint64_t>(), S.emit_keys_alt.as<uint64_t>());
   cub::DoubleBuffer<int32_t> dv(S.emit_idx.as<int32_t>(), S.emit_idx_alt.as<int32_t>());
@@ -494,6 +502,7 @@ bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
   int32_t* head = S.seg_head.as<int32_t>();
   int32_t* pos = S.seg_pos.as<int32_t>();
   k_heads<<<grid_for(n_emit), kThreads, 0, st>>>(dk.Current(), n_emit, head);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_CUDA(cudaMemsetAsync(head + n_emit, 0, sizeof(int32_t), st));
   tmp = 0;
@@ -509,6 +518,7 @@ bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
   k_segsum<<<grid_for(n_emit), kThreads, 0, st>>>(dk.Current(), dv.Current(), S.emit_vals.as<double>(),
                                                  head, pos, n_emit, S.C_row.as<int32_t>(),
                                                  S.C_col.as<int32_t>(), S.C_val.as<double>());
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   S.nnzC = nC;
   return BAL_OK;
@@ -545,6 +555,7 @@ bal_status compact_f64(Scene& S, const double* in, const uint8_t* flag, int64_t 
 
 bal_status launch_dinv(Scene& S, cudaStream_t st) {
   k_dinv<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -552,13 +563,19 @@ bal_status launch_dinv(Scene& S, cudaStream_t st) {
 bal_status make_f32_copy(Scene& S, cudaStream_t st) {
   const int64_t n9 = 9 * (int64_t)S.d.nv;
   k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.D, S.D32);
+  ::bal::note_launch();
   k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.Dinv, S.Dinv32);
-  if (S.d.nnzL)
+  ::bal::note_launch();
+  if (S.d.nnzL) {
     k_convert<float><<<grid_for(9 * S.d.nnzL), kThreads, 0, st>>>(9 * S.d.nnzL, S.d.Lval, S.Lval32);
+    ::bal::note_launch();
+  }
   BAL_TRY(buf_reserve(S.C_val32, sizeof(float) * 9 * (S.nnzC + 1)));
-  if (S.nnzC)
+  if (S.nnzC) {
     k_convert<float><<<grid_for(9 * S.nnzC), kThreads, 0, st>>>(9 * S.nnzC, S.C_val.as<double>(),
                                                                  S.C_val32.as<float>());
+    ::bal::note_launch();
+  }
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -595,6 +612,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
   const int64_t n3 = 3 * (int64_t)S.d.nv;
   BAL_TRY(spmv(S, x, S.pcg_q, st));
   k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   double rn, bn;
   BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
@@ -611,6 +629,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
   const Sys<float> A = sys32(S);
   while (!converged && passes < S.prm.mixed_max_refine && total < max_it) {
     k_scale_to_f32<<<grid_for(n3), kThreads, 0, st>>>(n3, 1.0 / rn, S.pcg_r, S.b32);
+    ::bal::note_launch();
     BAL_CUDA(cudaMemsetAsync(S.x32, 0, sizeof(float) * n3, st));
     BAL_LAUNCH_CHECK();
     PcgScalars h;
@@ -621,9 +640,11 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     total += h.it;
     passes += 1;
     k_refine_update<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, S.x32, x);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
     BAL_TRY(spmv(S, x, S.pcg_q, st));
     k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
+    ::bal::note_launch();
     BAL_LAUNCH_CHECK();
     BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
     double res[2];
@@ -659,6 +680,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
 static bal_status warm_start(Scene& S, const double* b, double* x, int* iters, int* ngroups,
                              cudaStream_t st) {
   k_groups<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d.Lambda, S.d.nv, S.group);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   Sys<double> A = sys64(S);
   A.O.group = S.group;
@@ -732,6 +754,7 @@ __global__ void __launch_bounds__(NT) k_resid(Dev S, const double* __restrict__ 
 
 bal_status launch_residual_norm(Scene& S, const double* b, const double* y, cudaStream_t st) {
   k_resid<256><<<kRedBlocks, 256, 0, st>>>(S.d, b, y, S.partials);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(finish_reduce_offset(S, 0, kRedBlocks, 8, RED_SUM, st));
   BAL_TRY(finish_reduce_offset(S, kRedBlocks, kRedBlocks, 9, RED_SUM, st));

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(NT) k_surf_max_norm(Dev S, const double* __res
 
 bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y, cudaStream_t st) {
   k_make_y<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, xt, vt, S.grav[0], S.grav[1], S.grav[2], y);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
@@ -58,18 +59,21 @@ bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y
 bal_status launch_axpy(Scene& S, int64_t n, double a, const double* x, const double* y, double* out,
                        cudaStream_t st) {
   k_axpy<<<grid_for(n), kThreads, 0, st>>>(n, a, x, y, out);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
 
 bal_status launch_dot(Scene& S, int64_t n, const double* a, const double* b, int slot, cudaStream_t st) {
   k_dot<256><<<kRB, 256, 0, st>>>(n, a, b, S.partials);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, kRB, slot, RED_SUM, st);
 }
 
 bal_status launch_surf_max_norm(Scene& S, const double* d, int slot, cudaStream_t st) {
   k_surf_max_norm<256><<<kRB, 256, 0, st>>>(S.d, d, S.partials);
+  ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, kRB, slot, RED_MAX, st);
 }
