@@ -101,16 +101,40 @@ class Clocks:
 FP64_PEAK_TFLOPS = 1.128
 
 
-def spmv_flops(nv, nnzL, nnzC):
-    """FP64 flops of one symmetric SpMV: 2 x 9 FMA per stored off-diagonal block
-    (block and transpose), 9 FMA per diagonal block."""
-    return 36.0 * (nnzL + nnzC) + 18.0 * nv
+PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 
-def spmv_bytes(nv, nnzL, nnzC, p=8):
-    """Algorithmic bytes of one symmetric SpMV: D, L and C blocks, their column
-    indices, the row pointer, and one read of v plus one write of y."""
-    return (nv + nnzL + nnzC) * 9 * p + (nnzL + nnzC) * 4 + (nv + 1) * 4 + 2 * 3 * nv * p
+def spmv_kernel_bytes(precision, nv, nnzL, nnzC):
+    """Name and algorithmic bytes of one launch of the timed SpMV kernel of a
+    PCG iteration (every stored value, index and vector entry moved once).
+
+    fp64 / mixed: the off-diagonal product (k_pcg_offdiag): lower blocks with
+    their row and column index, one read of p, q read and written once.
+    df64: the gather product (k_dd_spmv, double-floats of 8 bytes): diagonal and
+    lower blocks, the column index of the row-ordered list and the block and
+    row index of the column-ordered list, two row-pointer arrays, p read once,
+    q written once."""
+    nb = nnzL + nnzC
+    if precision == "df64":
+        ptrs = 2 * (nv + 1) * 4 * (2 if nnzC else 1)
+        return "k_dd_spmv (gather H p, double-float)", (nv + nb) * 72 + nb * 12 + ptrs + 2 * 24 * nv
+    p = 4 if precision == "mixed" else 8
+    return "k_pcg_offdiag (symmetric off-diagonal blocks, atomics)", nb * (9 * p + 8) + 3 * 3 * nv * p
+
+
+def roofline_entry(precision, kname, achieved, peak, peak_kind, byts, ms, n, nv, nnzL, nnzC):
+    out = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+           "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+           "traffic": None, "bytes_per_launch": byts, "ms_per_launch": round(ms, 5),
+           "timed_launches": n, "nnz_L": nnzL, "nnz_C_last": nnzC}
+    if precision == "fp64":
+        flops = 36.0 * (nnzL + nnzC)
+        tf = flops / (ms * 1e-3) / 1e12
+        out["alu"] = {"bound": "alu", "unit": "FP64 TFLOP/s", "achieved": round(tf, 4),
+                      "peak": FP64_PEAK_TFLOPS, "frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                      "peak_kind": "measured (FP64 FMA probe, 148 SMs x 2 DFMA/clk)"}
+    return out
 
 
 def run_pcg_only(args):
@@ -123,7 +147,7 @@ def run_pcg_only(args):
     dev = torch.device("cuda", 0)
     sc = scenes.scene_by_name(args.scene)
     params = bal.default_params(pcg_stall_window=1 << 30,
-                                precision=bal.PREC_MIXED if args.precision == "mixed" else bal.PREC_FP64,
+                                precision=PRECISIONS[args.precision],
                                 mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
@@ -135,6 +159,7 @@ def run_pcg_only(args):
     sol = torch.zeros_like(b)
     S.pcg_solve(b, sol, 0.0, 20)
     times = []
+    S.kernel_timing(True)
     for _ in range(max(args.steps, 1)):
         sol.zero_()
         torch.cuda.synchronize()
@@ -144,10 +169,15 @@ def run_pcg_only(args):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / max(info["iters"], 1))
+    k_ms, k_n = S.kernel_timing(False)
     ms = statistics.median(times)
+    kname, byts = spmv_kernel_bytes(args.precision, sc.n_verts, view["nnz_L"], view["nnz_C"])
+    kms = k_ms / max(k_n, 1)
     return {"mode": "pcg", "scene": args.scene, "precision": args.precision,
             "iters_per_solve": args.pcg_iters, "ms_per_iter": round(ms, 4),
-            "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "n_verts": sc.n_verts}
+            "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "n_verts": sc.n_verts,
+            "spmv_kernel": kname, "spmv_ms_per_launch": round(kms, 5),
+            "spmv_gbs": round(byts / (kms * 1e-3) / 1e9, 1), "spmv_bytes": byts}
 
 
 def run_ours(args, rank, world):
@@ -161,7 +191,7 @@ def run_ours(args, rank, world):
     params = bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
                                 newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
                                 pcg_max_iter=30000,
-                                precision=bal.PREC_MIXED if args.precision == "mixed" else bal.PREC_FP64)
+                                precision=PRECISIONS[args.precision])
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
@@ -185,6 +215,7 @@ def run_ours(args, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     timed = []
     launches0 = bal.launch_count()
+    S.kernel_timing(True)
     with Clocks(dev.index) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -192,6 +223,7 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
     launches = bal.launch_count() - launches0
+    k_ms, k_n = S.kernel_timing(False)
     for k, t in enumerate(timed):
         progress(f"timed {k}", t)
     if world > 1:
@@ -219,23 +251,12 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
 
-    # SpMV roofline on the last assembled Hessian (matrix > L2 at this size)
+    # roofline of the dominant kernel: the SpMV kernel of each PCG iteration,
+    # timed per launch with CUDA events on the solve stream during the timed region
     view = S.assemble_hessian(x)
     nv, nnzL, nnzC = sc.n_verts, view["nnz_L"], view["nnz_C"]
-    vec = torch.randn(3 * nv, dtype=torch.float64, device=dev)
-    out = torch.empty_like(vec)
-    for _ in range(3):
-        S.spmv(vec, out)
-    reps = 50
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(reps):
-        S.spmv(vec, out)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    spmv_ms = s0.elapsed_time(s1) / reps
-    byts = spmv_bytes(nv, nnzL, nnzC)
+    kname, byts = spmv_kernel_bytes(args.precision, nv, nnzL, nnzC)
+    spmv_ms = k_ms / max(k_n, 1)
     peak, peak_kind = peaks()
     achieved = byts / (spmv_ms * 1e-3) / 1e9
     # PCG-only iteration rate on the same system (fixed iteration count)
@@ -275,7 +296,7 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic (seeded procedural scene, no paper meshes)",
         "config": {
             "workload": f"{sc.name}: {sc.n_tets} tets, {sc.n_verts} verts, h=1/30 s, dhat=1e-3 m",
@@ -296,17 +317,8 @@ def run_ours(args, rank, world):
                               for k in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")},
         "e2e": {"value": round(e2e_val, 2), "unit": "PCG iter/s",
                 "h2d_bytes_per_step": 2 * 3 * nv * 8, "d2h_bytes_per_step": 2 * 3 * nv * 8},
-        "roofline": {"kernel": "bal_spmv (diag + off-diagonal blocks, FP64)", "bound": "hbm",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "traffic": None, "bytes_per_launch": byts, "ms_per_launch": round(spmv_ms, 4),
-                     "nnz_L": nnzL, "nnz_C": nnzC,
-                     "alu": {"bound": "alu", "unit": "FP64 TFLOP/s",
-                             "achieved": round(spmv_flops(nv, nnzL, nnzC) / (spmv_ms * 1e-3) / 1e12, 4),
-                             "peak": FP64_PEAK_TFLOPS,
-                             "frac": round(spmv_flops(nv, nnzL, nnzC) / (spmv_ms * 1e-3) / 1e12
-                                           / FP64_PEAK_TFLOPS, 4),
-                             "peak_kind": "measured (FP64 FMA probe, 148 SMs x 2 DFMA/clk)"}},
+        "roofline": roofline_entry(args.precision, kname, achieved, peak, peak_kind, byts, spmv_ms,
+                                   k_n, nv, nnzL, nnzC),
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "status": [t["status"] for t in timed],
@@ -392,7 +404,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scene", default="chain_net_shells")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
     ap.add_argument("--newton-max", type=int, default=20,

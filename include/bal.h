@@ -43,7 +43,11 @@ typedef enum {
   BAL_ERR_STATE = 8           /* call order violated (e.g. solve before assemble) */
 } bal_status;
 
-typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1 } bal_precision;
+/* FP64: every PCG operation in FP64. MIXED: FP32 inner PCG with FP64 iterative
+ * refinement. DF64: PCG recurrences in double-float arithmetic (pairs of FP32,
+ * ~47-bit significand) with FP64 residuals deciding convergence; falls back to
+ * FP64 for a matrix with an entry beyond 1e36. */
+typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2 } bal_precision;
 typedef enum { BAL_PRECOND_BJ = 0, BAL_PRECOND_BJ_WARMSTART = 1 } bal_precond;
 
 /* Solver and schedule parameters. bal_default_params follows the paper: Newton
@@ -137,11 +141,12 @@ typedef struct {
   double rel_residual_r0;     /* ||b - H x|| / ||r_0|| */
   int32_t stagnated;          /* 1 if stopped by the stagnation window */
   int32_t converged;          /* 1 if the tolerance was met */
-  int32_t refine_passes;      /* mixed precision: FP64 refinement passes */
+  int32_t refine_passes;      /* mixed / df64 precision: FP64 refinement passes */
   int32_t warm_iters;         /* warm start: subdomain PCG iterations */
   int32_t n_groups;           /* warm start: stiffness groups */
   int32_t negative_curvature; /* adjoint: 1 if the unprojected H was indefinite and the
                                  projected H was used instead */
+  int32_t precision_used;     /* bal_precision the solve ran in */
 } bal_solve_info;
 
 typedef struct {
@@ -188,6 +193,16 @@ BAL_API bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params
                             bal_scene** out);
 BAL_API bal_status bal_destroy_scene(bal_scene* scene);
 BAL_API bal_status bal_set_params(bal_scene* scene, const bal_params* params);
+/* Per-launch timing of the SpMV kernel of every PCG iteration (the dominant
+ * kernel of a solve: the off-diagonal product of the FP64 / mixed solvers, the
+ * gather product of the double-float one) with CUDA events recorded on the
+ * solve's stream. Returns in total_ms / launches (either may be NULL) the sum
+ * of the durations and the number of timed launches since the previous call,
+ * resets both, and enables (enable != 0) or disables timing for later solves.
+ * Not in the paper: measurement support. */
+BAL_API bal_status bal_kernel_timing(bal_scene* scene, int32_t enable, double* total_ms,
+                                     int64_t* launches);
+
 BAL_API bal_status bal_get_params(const bal_scene* scene, bal_params* out);
 /* Host copies of the static pattern: row_ptr [n_verts+1], col [nnz_L]; either
  * may be NULL to query nnz only. */

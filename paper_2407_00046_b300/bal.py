@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libbal.so")
 OK = 0
 STATUS = {0: "OK", 1: "ARG", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
           6: "CUDA", 7: "LINE_SEARCH", 8: "STATE"}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
 PRECOND_BJ, PRECOND_BJ_WARMSTART = 0, 1
 
 
@@ -70,7 +70,7 @@ class SolveInfo(C.Structure):
                 ("rel_residual_r0", C.c_double), ("stagnated", C.c_int32),
                 ("converged", C.c_int32), ("refine_passes", C.c_int32),
                 ("warm_iters", C.c_int32), ("n_groups", C.c_int32),
-                ("negative_curvature", C.c_int32)]
+                ("negative_curvature", C.c_int32), ("precision_used", C.c_int32)]
 
 
 class NewtonInfo(C.Structure):
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         "bal_destroy_scene": ([P], C.c_int),
         "bal_set_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_get_params": ([P, C.POINTER(Params)], C.c_int),
+        "bal_kernel_timing": ([P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
         "bal_static_pattern": ([P, C.POINTER(C.c_int64), P, P], C.c_int),
         "bal_get_mass": ([P, P], C.c_int),
         "bal_step_begin": ([P, P, P, P], C.c_int),
@@ -234,6 +235,13 @@ class Scene:
             setattr(p, k, v)
         _check(load().bal_set_params(self._h, C.byref(p)))
         self.params = p
+
+    def kernel_timing(self, enable: bool):
+        """(total ms, launches) of the timed SpMV kernel of each PCG iteration
+        since the previous call; resets them and switches timing on or off."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(load().bal_kernel_timing(self._h, int(bool(enable)), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def get_params(self) -> Params:
         p = Params()

@@ -40,6 +40,17 @@ bal_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
   return BAL_ERR_CUDA;
 }
 
+bal_status kt_collect(Scene& S, int n) {
+  if (!S.ktime) return BAL_OK;
+  for (int k = 0; k < n; ++k) {
+    float ms = 0.f;
+    BAL_CUDA(cudaEventElapsedTime(&ms, S.kev[2 * k], S.kev[2 * k + 1]));
+    S.kt_ms += ms;
+    S.kt_n += 1;
+  }
+  return BAL_OK;
+}
+
 bal_status buf_reserve(Buf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return BAL_OK;
   if (b.p) {
@@ -216,6 +227,7 @@ bal_status assemble(Scene& S, const double* x, double* g, cudaStream_t st) {
   BAL_TRY(launch_dinv(S, st));
   S.assembled = true;
   S.f32_valid = false;
+  S.dd_valid = false;
   return BAL_OK;
 }
 
@@ -770,11 +782,16 @@ bal_status bal_destroy_scene(bal_scene* sc) {
   if (!sc) return BAL_OK;
   Scene& S = sc->S;
   for (void* p : S.owned) cudaFree(p);
+  for (cudaEvent_t& e : S.kev)
+    if (e) cudaEventDestroy(e);
   Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_keys_alt, &S.emit_idx,
                  &S.emit_idx_alt, &S.emit_vals, &S.seg_head, &S.seg_pos, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
-                 &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d};
+                 &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d,
+                 &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos,
+                 &S.dd_D, &S.dd_Dinv, &S.dd_R, &S.dd_C, &S.dd_vec, &S.cr_rows, &S.cr_ptr, &S.cr_ent,
+                 &S.cr_src, &S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_cnt, &S.cr_num};
   for (Buf* b : bufs) buf_free(*b);
   delete sc;
   return BAL_OK;
@@ -783,11 +800,25 @@ bal_status bal_destroy_scene(bal_scene* sc) {
 bal_status bal_set_params(bal_scene* sc, const bal_params* p) {
   BAL_TRY(check_scene(sc));
   if (!p || !(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
+      p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1)) {
     set_error("bal_set_params: invalid parameters");
     return BAL_ERR_ARG;
   }
   sc->S.prm = *p;
+  return BAL_OK;
+}
+
+bal_status bal_kernel_timing(bal_scene* sc, int32_t enable, double* total_ms, int64_t* launches) {
+  BAL_TRY(check_scene(sc));
+  Scene& S = sc->S;
+  if (total_ms) *total_ms = S.kt_ms;
+  if (launches) *launches = S.kt_n;
+  S.kt_ms = 0;
+  S.kt_n = 0;
+  if (enable && !S.kev[0])
+    for (cudaEvent_t& e : S.kev) BAL_CUDA(cudaEventCreate(&e));
+  S.ktime = enable != 0;
   return BAL_OK;
 }
 

@@ -1,0 +1,674 @@
+// Block-Jacobi PCG with double-float recurrences (Sec. 4.2, App. B; the
+// precision is this library's choice for B300, whose FP64 pipe runs at ~1/58 of
+// its FP32 rate).
+//
+// The same CG iteration as the FP64 solver in matrix.cu, with H, D^{-1} and the
+// vectors held as double-floats (dd.cuh, ~47-bit significand) so that every
+// iteration runs in FP32 arithmetic and is bound by memory traffic. FP64
+// decides convergence: the initial residual r = b - H x and the final one are
+// computed with the FP64 matrix; if the recurrence reports convergence but the
+// FP64 residual is still above tolerance, CG restarts from the FP64 residual
+// (iterative refinement), at most mixed_max_refine times.
+//
+// H v keeps the paper's symmetric storage (D, L, C; Sec. 5.1) but evaluates it
+// as a gather, one thread per row, with no atomics, so the result is
+// deterministic. The static lower blocks sit in a sliced-ELL layout: 32 rows
+// per slice, entry k of the 32 rows adjacent in memory and the 9 entries of a
+// block 32 values apart, so one warp reads a slice with coalesced loads. Row i
+// sums D_i v_i, its own blocks L_ij v_j, then the transposes L_ki^T v_k of the
+// blocks stored in later rows k with column i (the column-side list holds their
+// value positions); on a lattice ordering those also lie side by side for 32
+// adjacent rows, and their second read is served by L2. Contact blocks are
+// added by a second kernel over the rows they touch.
+#include <cub/cub.cuh>
+
+#include "dd.cuh"
+#include "scene.cuh"
+
+namespace bal {
+
+namespace {
+
+constexpr int kDdThreads = 256;
+constexpr int kDdWarps = kDdThreads / 32;
+constexpr int kDdBlocks = 8 * kNumSM;    // CTAs of the vector kernels
+constexpr double kDdRange = 1e36;        // entries beyond this stay in the FP64 solver
+
+struct DDSys {
+  const dd* D;            // [ns][9][32]
+  const dd* Dinv;         // [ns][9][32]
+  const int32_t* offR;    // [ns+1]
+  const int32_t* Rcol;    // [offR[ns]]
+  const dd* R;            // sliced lower blocks (+ one zero chunk)
+  const int32_t* offT;    // [ns+1]
+  const int32_t* Tpos;    // [offT[ns]]
+  const int32_t* Tsrc;    // [offT[ns]]
+  int nv, ns;
+};
+
+struct DDContact {
+  const int32_t* rows;    // [n] unique rows
+  const int32_t* ptr;     // [n+1]
+  const int32_t* ent;     // [2 nC] 2c + (1 if C_c^T is applied)
+  const int32_t* src;     // [2 nC] source vertex
+  const dd* C;            // [nC][9]
+  int n;
+};
+
+// entry e of the block at value position b of the sliced storage is b[32 e]
+__device__ __forceinline__ dd3 mv_sliced(const dd* __restrict__ b, dd3 v) {
+  dd B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = b[32 * k];
+  return dd3{dd_fma(B[2], v.z, dd_fma(B[1], v.y, dd_mul(B[0], v.x))),
+             dd_fma(B[5], v.z, dd_fma(B[4], v.y, dd_mul(B[3], v.x))),
+             dd_fma(B[8], v.z, dd_fma(B[7], v.y, dd_mul(B[6], v.x)))};
+}
+__device__ __forceinline__ dd3 mtv_sliced(const dd* __restrict__ b, dd3 v) {
+  dd B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = b[32 * k];
+  return dd3{dd_fma(B[6], v.z, dd_fma(B[3], v.y, dd_mul(B[0], v.x))),
+             dd_fma(B[7], v.z, dd_fma(B[4], v.y, dd_mul(B[1], v.x))),
+             dd_fma(B[8], v.z, dd_fma(B[5], v.y, dd_mul(B[2], v.x)))};
+}
+// value position of vertex i's block in a slice-major [ns][9][32] array
+__device__ __forceinline__ int64_t slice_base(int i) { return (int64_t)(i >> 5) * 9 * 32 + (i & 31); }
+
+__device__ __forceinline__ void dd3_acc(dd3& a, dd3 b) {
+  a.x = dd_add(a.x, b.x);
+  a.y = dd_add(a.y, b.y);
+  a.z = dd_add(a.z, b.z);
+}
+
+// D or D^-1 (FP64, [nv][9]) into the slice-major double-float layout
+__global__ void k_dd_slices(int nv, const double* __restrict__ a, dd* __restrict__ out, unsigned int* bad) {
+  const int64_t n = 9 * (int64_t)nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / 9), e = (int)(t % 9);
+    const double v = a[t];
+    if (!(fabs(v) <= kDdRange)) atomicAdd(bad, 1u);
+    out[slice_base(i) + 32 * e] = dd_from(v);
+  }
+}
+// L values (FP64, CSR slot order [nL][9]) into their sliced positions
+__global__ void k_dd_scatter(int64_t nL, const double* __restrict__ L, const int32_t* __restrict__ pos,
+                             dd* __restrict__ R, unsigned int* bad) {
+  const int64_t n = 9 * nL;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / 9;
+    const int e = (int)(t % 9);
+    const double v = L[t];
+    if (!(fabs(v) <= kDdRange)) atomicAdd(bad, 1u);
+    R[(int64_t)pos[s] + 32 * e] = dd_from(v);
+  }
+}
+__global__ void k_to_dd(int64_t n, const double* __restrict__ a, dd* __restrict__ b, unsigned int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    if (!(fabs(v) <= kDdRange)) atomicAdd(bad, 1u);
+    b[i] = dd_from(v);
+  }
+}
+
+// directed contact entries: e < nC applies C_e to row C_row[e]; e >= nC applies
+// C_{e-nC}^T to row C_col[e-nC]
+__global__ void k_crow_keys(const int32_t* __restrict__ crow, const int32_t* __restrict__ ccol, int nC,
+                            int32_t* __restrict__ key, int32_t* __restrict__ val) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * nC; e += gridDim.x * blockDim.x) {
+    const bool tr = e >= nC;
+    const int c = tr ? e - nC : e;
+    key[e] = tr ? ccol[c] : crow[c];
+    val[e] = 2 * c + (tr ? 1 : 0);
+  }
+}
+__global__ void k_crow_src(const int32_t* __restrict__ ent, const int32_t* __restrict__ crow,
+                           const int32_t* __restrict__ ccol, int n2, const int32_t* __restrict__ nrows,
+                           int32_t* __restrict__ src, int32_t* __restrict__ ptr) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += gridDim.x * blockDim.x) {
+    const int c = ent[e] >> 1;
+    src[e] = (ent[e] & 1) ? crow[c] : ccol[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ptr[*nrows] = n2;
+}
+
+__device__ inline bool dd_arrive_last(uint32_t* counter) {
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  return last;
+}
+
+template <int NT>
+__device__ inline double dd_sum_partials(const double* partials, int n) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) acc += ((volatile const double*)partials)[i];
+  return block_sum<double, NT>(acc);
+}
+
+__device__ inline void set_alpha(PcgScalars* P, double pq) {
+  P->pq = pq;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    P->done = 3;   // loss of positive definiteness or non-finite
+  } else {
+    P->alpha = P->rz / pq;
+    const dd a = dd_from(P->alpha);
+    P->alpha_hi = a.hi;
+    P->alpha_lo = a.lo;
+  }
+}
+
+__device__ __forceinline__ dd3 dinv_apply(const DDSys& A, int i, dd3 r) {
+  return mv_sliced(A.Dinv + slice_base(i), r);
+}
+
+// r = s * rf (FP64 residual scaled to unit norm), z = D^{-1} r, x = 0; rz, ||r||.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dd_init(DDSys A, const double* __restrict__ rf, double s,
+                                                dd* __restrict__ x, dd* __restrict__ r,
+                                                dd* __restrict__ z, PcgScalars* P, double* partials,
+                                                double tol) {
+  dd rz{0.f, 0.f}, rr{0.f, 0.f};
+  for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
+    const dd3 ri{dd_from(s * rf[3 * (int64_t)i]), dd_from(s * rf[3 * (int64_t)i + 1]),
+                 dd_from(s * rf[3 * (int64_t)i + 2])};
+    const dd3 zi = dinv_apply(A, i, ri);
+    dd3_st(r, i, ri);
+    dd3_st(z, i, zi);
+    dd3_st(x, i, dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}});
+    rz = dd_add(rz, dd3_dot(ri, zi));
+    rr = dd_add(rr, dd3_dot(ri, ri));
+  }
+  rz = dd_block_sum<NT>(rz);
+  rr = dd_block_sum<NT>(rr);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = dd_to(rz);
+    partials[gridDim.x + blockIdx.x] = dd_to(rr);
+  }
+  if (dd_arrive_last(&P->counter)) {
+    const double trz = dd_sum_partials<NT>(partials, gridDim.x);
+    const double trr = dd_sum_partials<NT>(partials + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      P->rz = trz;
+      P->r0norm = sqrt(trr);
+      P->rnorm = P->r0norm;
+      P->bnorm = P->r0norm;
+      P->best = sqrt(fmax(trz, 0.0));
+      P->best_it = 0;
+      P->it = 0;
+      P->tol_abs = tol * P->r0norm;
+      P->stagnated = 0;
+      P->converged = (P->r0norm == 0.0) ? 1 : 0;
+      P->done = P->converged;
+      P->beta = 0.0;
+      if (!(isfinite(trz) && isfinite(trr))) P->done = 2;
+      P->counter = 0;
+    }
+  }
+}
+
+// p = z + beta p (p = z on the first iteration)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dd_dir(int nv, const dd* __restrict__ z, dd* __restrict__ p,
+                                               const PcgScalars* P) {
+  if (P->done) return;
+  const bool first = P->it == 0;
+  const dd beta{P->beta_hi, P->beta_lo};
+  for (int i = blockIdx.x * NT + threadIdx.x; i < nv; i += gridDim.x * NT) {
+    const dd3 zi = dd3_ld(z, i);
+    dd3_st(p, i, first ? zi : dd3_axpy(beta, dd3_ld(p, i), zi));
+  }
+}
+
+// q = (D + L + L^T) p, one warp per slice; partial sums of p^T q. With
+// finalize, the last CTA sets alpha = rz / p^T q (no contact blocks).
+__global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __restrict__ p,
+                                                        dd* __restrict__ q, PcgScalars* P,
+                                                        double* partials, int finalize) {
+  if (P->done) return;
+  const int lane = threadIdx.x & 31;
+  dd pq{0.f, 0.f};
+  for (int s = blockIdx.x * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += gridDim.x * kDdWarps) {
+    const int i = 32 * s + lane;
+    const bool own = i < A.nv;
+    const dd3 pi = own ? dd3_ld(p, i) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+    dd3 acc = mv_sliced(A.D + slice_base(i), pi);
+    const int r1 = A.offR[s + 1];
+#pragma unroll 2
+    for (int idx = A.offR[s] + lane; idx < r1; idx += 32)
+      dd3_acc(acc, mv_sliced(A.R + 9 * (int64_t)(idx - lane) + lane, dd3_ld(p, A.Rcol[idx])));
+    const int t1 = A.offT[s + 1];
+#pragma unroll 2
+    for (int idx = A.offT[s] + lane; idx < t1; idx += 32)
+      dd3_acc(acc, mtv_sliced(A.R + A.Tpos[idx], dd3_ld(p, A.Tsrc[idx])));
+    if (own) {
+      dd3_st(q, i, acc);
+      pq = dd_add(pq, dd3_dot(pi, acc));
+    }
+  }
+  pq = dd_block_sum<kDdThreads>(pq);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dd_to(pq);
+  if (!finalize) return;
+  if (dd_arrive_last(&P->counter)) {
+    const double tpq = dd_sum_partials<kDdThreads>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      set_alpha(P, tpq);
+      P->counter = 0;
+    }
+  }
+}
+
+// q_i += sum of the contact blocks of row i (both orientations) applied to p;
+// partial sums of p_i . (contact part of q_i); the last CTA adds the n_prev
+// partials of k_dd_spmv and sets alpha.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dd_contact(DDContact Cr, const dd* __restrict__ p,
+                                                   dd* __restrict__ q, PcgScalars* P, double* partials,
+                                                   int n_prev) {
+  if (P->done) return;
+  dd pq{0.f, 0.f};
+  for (int t = blockIdx.x * NT + threadIdx.x; t < Cr.n; t += gridDim.x * NT) {
+    const int i = Cr.rows[t];
+    dd3 acc{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+    for (int e = Cr.ptr[t]; e < Cr.ptr[t + 1]; ++e) {
+      const int ent = Cr.ent[e];
+      const dd* B = Cr.C + 9 * (int64_t)(ent >> 1);
+      const dd3 v = dd3_ld(p, Cr.src[e]);
+      dd3_acc(acc, (ent & 1) ? dd3_mtv(B, v) : dd3_mv(B, v));
+    }
+    dd3 qi = dd3_ld(q, i);
+    dd3_acc(qi, acc);
+    dd3_st(q, i, qi);
+    pq = dd_add(pq, dd3_dot(dd3_ld(p, i), acc));
+  }
+  pq = dd_block_sum<NT>(pq);
+  if (threadIdx.x == 0) partials[n_prev + blockIdx.x] = dd_to(pq);
+  if (dd_arrive_last(&P->counter)) {
+    const double tpq = dd_sum_partials<NT>(partials, n_prev + gridDim.x);
+    if (threadIdx.x == 0) {
+      set_alpha(P, tpq);
+      P->counter = 0;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, z = D^{-1} r; rz, ||r||; convergence, stagnation, beta
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, const dd* __restrict__ p,
+                                                  const dd* __restrict__ q, dd* __restrict__ r,
+                                                  dd* __restrict__ z, PcgScalars* P, double* partials) {
+  if (P->done) return;
+  const dd alpha{P->alpha_hi, P->alpha_lo};
+  const dd malpha = dd_neg(alpha);
+  dd rz{0.f, 0.f}, rr{0.f, 0.f};
+  for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
+    dd3_st(x, i, dd3_axpy(alpha, dd3_ld(p, i), dd3_ld(x, i)));
+    const dd3 ri = dd3_axpy(malpha, dd3_ld(q, i), dd3_ld(r, i));
+    const dd3 zi = dinv_apply(A, i, ri);
+    dd3_st(r, i, ri);
+    dd3_st(z, i, zi);
+    rz = dd_add(rz, dd3_dot(ri, zi));
+    rr = dd_add(rr, dd3_dot(ri, ri));
+  }
+  rz = dd_block_sum<NT>(rz);
+  rr = dd_block_sum<NT>(rr);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = dd_to(rz);
+    partials[gridDim.x + blockIdx.x] = dd_to(rr);
+  }
+  if (dd_arrive_last(&P->counter)) {
+    const double trz = dd_sum_partials<NT>(partials, gridDim.x);
+    const double trr = dd_sum_partials<NT>(partials + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      const int it = P->it + 1;
+      const double rn = sqrt(trr);
+      const double pn = sqrt(fmax(trz, 0.0));
+      P->it = it;
+      P->rnorm = rn;
+      if (pn < P->best) {
+        P->best = pn;
+        P->best_it = it;
+      }
+      if (!isfinite(rn)) {
+        P->done = 2;
+      } else if (rn <= P->tol_abs) {
+        P->done = 1;
+        P->converged = 1;
+      } else if (it - P->best_it >= P->window) {
+        P->done = 1;
+        P->stagnated = 1;
+      } else if (it >= P->max_it) {
+        P->done = 1;
+      }
+      P->beta = trz / P->rz;
+      const dd b = dd_from(P->beta);
+      P->beta_hi = b.hi;
+      P->beta_lo = b.lo;
+      P->rz = trz;
+      P->counter = 0;
+    }
+  }
+}
+
+// x += s * e (FP64 += double-float)
+__global__ void k_dd_accumulate(int64_t n, double s, const dd* __restrict__ e, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += s * dd_to(e[i]);
+}
+
+// Sliced layout of the static lower blocks from the host CSR copy (once).
+bal_status build_sell(Scene& S) {
+  const int nv = S.d.nv;
+  const int64_t nL = S.d.nnzL;
+  const int ns = (nv + 31) / 32;
+  const std::vector<int32_t>& rp = S.row_ptr_h;
+  const std::vector<int32_t>& col = S.col_h;
+  // column lists (ascending row) of the lower blocks
+  std::vector<int32_t> cp(nv + 1, 0);
+  for (int64_t s = 0; s < nL; ++s) cp[col[s] + 1]++;
+  for (int v = 0; v < nv; ++v) cp[v + 1] += cp[v];
+  std::vector<int32_t> cslot(nL > 0 ? nL : 1), crow(nL > 0 ? nL : 1);
+  {
+    std::vector<int32_t> fill(cp.begin(), cp.end() - 1);
+    for (int r = 0; r < nv; ++r)
+      for (int32_t s = rp[r]; s < rp[r + 1]; ++s) {
+        const int32_t e = fill[col[s]]++;
+        cslot[e] = s;
+        crow[e] = r;
+      }
+  }
+  std::vector<int32_t> offR(ns + 1, 0), offT(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) {
+    int lr = 0, lt = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int i = 32 * s + l;
+      if (i >= nv) break;
+      lr = std::max(lr, rp[i + 1] - rp[i]);
+      lt = std::max(lt, cp[i + 1] - cp[i]);
+    }
+    if ((int64_t)offR[s] + 32 * (int64_t)lr > (INT32_MAX / 9 - 64) ||
+        (int64_t)offT[s] + 32 * (int64_t)lt > INT32_MAX) {
+      set_error("df64 pcg: sliced storage exceeds 32-bit positions");
+      return BAL_ERR_CAPACITY;
+    }
+    offR[s + 1] = offR[s] + 32 * lr;
+    offT[s + 1] = offT[s] + 32 * lt;
+  }
+  const int64_t nR = offR[ns], nT = offT[ns];
+  const int32_t zero = 9 * (int32_t)nR;   // the zero chunk after the row-side chunks
+  std::vector<int32_t> Rcol(nR > 0 ? nR : 1), pos(nL > 0 ? nL : 1), Tpos(nT > 0 ? nT : 1), Tsrc(nT > 0 ? nT : 1);
+  // row side first: the column side refers to the value positions of later rows
+  for (int s = 0; s < ns; ++s) {
+    const int lr = (offR[s + 1] - offR[s]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int i = 32 * s + l;
+      const int len = i < nv ? rp[i + 1] - rp[i] : 0;
+      for (int k = 0; k < lr; ++k) {
+        const int32_t idx = offR[s] + 32 * k + l;
+        if (k < len) {
+          const int32_t slot = rp[i] + k;
+          Rcol[idx] = col[slot];
+          pos[slot] = 9 * (idx - l) + l;
+        } else {
+          Rcol[idx] = i < nv ? i : 0;   // a zero block times a valid entry
+        }
+      }
+    }
+  }
+  for (int s = 0; s < ns; ++s) {
+    const int lt = (offT[s + 1] - offT[s]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int i = 32 * s + l;
+      const int len = i < nv ? cp[i + 1] - cp[i] : 0;
+      for (int k = 0; k < lt; ++k) {
+        const int32_t idx = offT[s] + 32 * k + l;
+        if (k < len) {
+          Tpos[idx] = pos[cslot[cp[i] + k]];
+          Tsrc[idx] = crow[cp[i] + k];
+        } else {
+          Tpos[idx] = zero + l;
+          Tsrc[idx] = i < nv ? i : 0;
+        }
+      }
+    }
+  }
+  auto up = [&](Buf& b, const std::vector<int32_t>& v) -> bal_status {
+    BAL_TRY(buf_reserve(b, sizeof(int32_t) * v.size()));
+    BAL_CUDA(cudaMemcpy(b.p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
+    return BAL_OK;
+  };
+  BAL_TRY(up(S.sell_offR, offR));
+  BAL_TRY(up(S.sell_offT, offT));
+  BAL_TRY(up(S.sell_Rcol, Rcol));
+  BAL_TRY(up(S.sell_Tpos, Tpos));
+  BAL_TRY(up(S.sell_Tsrc, Tsrc));
+  BAL_TRY(up(S.sell_pos, pos));
+  const size_t nRval = 9 * (size_t)(nR + 32), nDval = (size_t)ns * 9 * 32;
+  BAL_TRY(buf_reserve(S.dd_R, sizeof(dd) * nRval));
+  BAL_TRY(buf_reserve(S.dd_D, sizeof(dd) * nDval));
+  BAL_TRY(buf_reserve(S.dd_Dinv, sizeof(dd) * nDval));
+  BAL_CUDA(cudaMemset(S.dd_R.p, 0, sizeof(dd) * nRval));   // padding and the zero chunk stay zero
+  BAL_CUDA(cudaMemset(S.dd_D.p, 0, sizeof(dd) * nDval));
+  BAL_CUDA(cudaMemset(S.dd_Dinv.p, 0, sizeof(dd) * nDval));
+  BAL_TRY(buf_reserve(S.dd_vec, sizeof(dd) * 6 * 3 * (size_t)nv));
+  S.n_slices = ns;
+  S.sell_zero = zero;
+  S.sell_built = true;
+  return BAL_OK;
+}
+
+// contact rows of the current C: unique rows of C and C^T with their entries
+bal_status build_contact_rows(Scene& S, cudaStream_t st) {
+  const int nC = (int)S.nnzC, n2 = 2 * nC;
+  S.n_crows = 0;
+  if (nC == 0) return BAL_OK;
+  for (Buf* b : {&S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_src, &S.cr_rows, &S.cr_cnt,
+                 &S.cr_ent})
+    BAL_TRY(buf_reserve(*b, sizeof(int32_t) * n2));
+  BAL_TRY(buf_reserve(S.cr_ptr, sizeof(int32_t) * (n2 + 1)));
+  BAL_TRY(buf_reserve(S.cr_num, sizeof(int32_t)));
+  k_crow_keys<<<grid_for(n2), kThreads, 0, st>>>(S.C_row.as<int32_t>(), S.C_col.as<int32_t>(), nC,
+                                                 S.cr_key.as<int32_t>(), S.cr_val.as<int32_t>());
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  cub::DoubleBuffer<int32_t> dk(S.cr_key.as<int32_t>(), S.cr_key_alt.as<int32_t>());
+  cub::DoubleBuffer<int32_t> dv(S.cr_val.as<int32_t>(), S.cr_val_alt.as<int32_t>());
+  int bits = 1;
+  while (bits < 31 && (1 << bits) <= S.d.nv) ++bits;
+  size_t tmp = 0;
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, n2, 0, bits, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, n2, 0, bits, st));
+  int32_t* keys = dk.Current();
+  int32_t* num = S.cr_num.as<int32_t>();
+  BAL_CUDA(cudaMemsetAsync(S.cr_cnt.p, 0, sizeof(int32_t) * n2, st));
+  tmp = 0;
+  BAL_CUDA(cub::DeviceRunLengthEncode::Encode(nullptr, tmp, keys, S.cr_rows.as<int32_t>(),
+                                              S.cr_cnt.as<int32_t>(), num, n2, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceRunLengthEncode::Encode(S.cub_tmp.p, tmp, keys, S.cr_rows.as<int32_t>(),
+                                              S.cr_cnt.as<int32_t>(), num, n2, st));
+  tmp = 0;
+  BAL_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, S.cr_cnt.as<int32_t>(), S.cr_ptr.as<int32_t>(), n2, st));
+  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
+  BAL_CUDA(cub::DeviceScan::ExclusiveSum(S.cub_tmp.p, tmp, S.cr_cnt.as<int32_t>(), S.cr_ptr.as<int32_t>(), n2, st));
+  BAL_CUDA(cudaMemcpyAsync(S.cr_ent.p, dv.Current(), sizeof(int32_t) * n2, cudaMemcpyDeviceToDevice, st));
+  k_crow_src<<<grid_for(n2), kThreads, 0, st>>>(S.cr_ent.as<int32_t>(), S.C_row.as<int32_t>(),
+                                                S.C_col.as<int32_t>(), n2, num, S.cr_src.as<int32_t>(),
+                                                S.cr_ptr.as<int32_t>());
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  int32_t n = 0;
+  BAL_CUDA(cudaMemcpyAsync(&n, num, sizeof(n), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  S.n_crows = n;
+  return BAL_OK;
+}
+
+// double-float copies of the assembled H and D^{-1}; contact rows.
+// *in_range = false if an entry exceeds the FP32 exponent range.
+bal_status refresh_dd(Scene& S, bool* in_range, cudaStream_t st) {
+  const int nv = S.d.nv;
+  const int64_t nL = S.d.nnzL, nC = S.nnzC;
+  if (!S.sell_built) BAL_TRY(build_sell(S));
+  unsigned int* bad = reinterpret_cast<unsigned int*>(S.scal + 61);
+  BAL_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
+  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.D, S.dd_D.as<dd>(), bad);
+  ::bal::note_launch();
+  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.Dinv, S.dd_Dinv.as<dd>(), bad);
+  ::bal::note_launch();
+  if (nL) {
+    k_dd_scatter<<<grid_for(9 * nL), kThreads, 0, st>>>(nL, S.d.Lval, S.sell_pos.as<int32_t>(),
+                                                         S.dd_R.as<dd>(), bad);
+    ::bal::note_launch();
+  }
+  BAL_LAUNCH_CHECK();
+  if (nC) {
+    BAL_TRY(buf_reserve(S.dd_C, sizeof(dd) * 9 * (size_t)nC));
+    k_to_dd<<<grid_for(9 * nC), kThreads, 0, st>>>(9 * nC, S.C_val.as<double>(), S.dd_C.as<dd>(), bad);
+    ::bal::note_launch();
+    BAL_LAUNCH_CHECK();
+  }
+  BAL_TRY(build_contact_rows(S, st));
+  unsigned int nbad = 0;
+  BAL_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  *in_range = nbad == 0;
+  return BAL_OK;
+}
+
+DDSys dd_sys(Scene& S) {
+  DDSys A;
+  A.D = S.dd_D.as<dd>();
+  A.Dinv = S.dd_Dinv.as<dd>();
+  A.offR = S.sell_offR.as<int32_t>();
+  A.Rcol = S.sell_Rcol.as<int32_t>();
+  A.R = S.dd_R.as<dd>();
+  A.offT = S.sell_offT.as<int32_t>();
+  A.Tpos = S.sell_Tpos.as<int32_t>();
+  A.Tsrc = S.sell_Tsrc.as<int32_t>();
+  A.nv = S.d.nv;
+  A.ns = S.n_slices;
+  return A;
+}
+
+DDContact dd_contact(Scene& S) {
+  DDContact C;
+  C.rows = S.cr_rows.as<int32_t>();
+  C.ptr = S.cr_ptr.as<int32_t>();
+  C.ent = S.cr_ent.as<int32_t>();
+  C.src = S.cr_src.as<int32_t>();
+  C.C = S.dd_C.as<dd>();
+  C.n = S.n_crows;
+  return C;
+}
+
+}  // namespace
+
+bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it,
+                    bal_solve_info* info, cudaStream_t st) {
+  bool in_range = true;
+  if (!S.dd_valid) {
+    BAL_TRY(refresh_dd(S, &in_range, st));
+    S.dd_valid = in_range;
+  }
+  if (!in_range) {   // an entry outside the FP32 exponent range: the FP64 solver takes it
+    const int32_t keep = S.prm.precision, keep_pc = S.prm.precond;
+    S.prm.precision = BAL_PREC_FP64;
+    S.prm.precond = BAL_PRECOND_BJ;   // a requested warm start has already run
+    const bal_status s = pcg_solve(S, b, x, tol, max_it, info, st);
+    S.prm.precision = keep;
+    S.prm.precond = keep_pc;
+    if (info) info->precision_used = BAL_PREC_FP64;
+    return s;
+  }
+  const int nv = S.d.nv;
+  const int64_t n3 = 3 * (int64_t)nv;
+  const DDSys A = dd_sys(S);
+  const DDContact Cr = dd_contact(S);
+  dd* V = S.dd_vec.as<dd>();
+  dd *ex = V, *er = V + n3, *ez = V + 2 * n3, *ep = V + 3 * n3, *eq = V + 4 * n3;
+  const int gs = std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
+  const int gc = std::max(1, std::min((Cr.n + kDdThreads - 1) / kDdThreads, kMaxPartials / 2));
+  const bool has_c = Cr.n > 0;
+  double rn, bn;
+  BAL_TRY(residual_fp64(S, b, x, S.pcg_r, &rn, &bn, st));
+  const double r0 = rn;
+  int total = 0, passes = 0, stagnated = 0;
+  bool converged = rn <= tol * r0 || rn == 0.0;
+  while (!converged && passes <= S.prm.mixed_max_refine && total < max_it) {
+    // solve H e = r / ||r|| to tol * r0 / ||r||, then x += ||r|| e
+    PcgScalars init{};
+    init.max_it = max_it - total;
+    init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
+    BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_dd_init<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(A, S.pcg_r, 1.0 / rn, ex, er, ez, S.pcg,
+                                                            S.partials, tol * r0 / rn);
+    ::bal::note_launch();
+    BAL_LAUNCH_CHECK();
+    PcgScalars h{};
+    const int chunk = Scene::kTimedPerChunk;
+    int launched = 0, timed = 0;
+    for (;;) {
+      BAL_CUDA(cudaMemcpyAsync(&h, S.pcg, sizeof(h), cudaMemcpyDeviceToHost, st));
+      BAL_CUDA(cudaStreamSynchronize(st));
+      BAL_TRY(kt_collect(S, timed));
+      timed = 0;
+      if (h.done || launched >= init.max_it) break;
+      const int n = std::min(chunk, init.max_it - launched);
+      for (int k = 0; k < n; ++k) {
+        k_dd_dir<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(nv, ez, ep, S.pcg);
+        ::bal::note_launch();
+        kt_before(S, k, st);
+        k_dd_spmv<<<gs, kDdThreads, 0, st>>>(A, ep, eq, S.pcg, S.partials, has_c ? 0 : 1);
+        kt_after(S, k, st);
+        ++timed;
+        ::bal::note_launch();
+        if (has_c) {
+          k_dd_contact<kDdThreads><<<gc, kDdThreads, 0, st>>>(Cr, ep, eq, S.pcg, S.partials, gs);
+          ::bal::note_launch();
+        }
+        k_dd_update<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(A, ex, ep, eq, er, ez, S.pcg, S.partials);
+        ::bal::note_launch();
+      }
+      BAL_LAUNCH_CHECK();
+      launched += n;
+    }
+    if (h.done == 2 || h.done == 3) {
+      set_error("df64 pcg: %s at iteration %d", h.done == 2 ? "non-finite residual" : "p^T H p <= 0",
+                total + h.it);
+      return BAL_ERR_NAN;
+    }
+    total += h.it;
+    passes += 1;
+    stagnated = h.stagnated;
+    k_dd_accumulate<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, ex, x);
+    ::bal::note_launch();
+    BAL_LAUNCH_CHECK();
+    const double prev = rn;
+    BAL_TRY(residual_fp64(S, b, x, S.pcg_r, &rn, &bn, st));
+    if (!std::isfinite(rn)) {
+      set_error("df64 pcg: non-finite FP64 residual after pass %d", passes);
+      return BAL_ERR_NAN;
+    }
+    converged = rn <= tol * r0;
+    // a pass that ended by stagnation or the cap, or made no progress, ends the solve
+    if (!h.converged || !(rn < 0.99 * prev) || h.it == 0) break;
+  }
+  if (info) {
+    info->iters = total;
+    info->rel_residual = bn > 0 ? rn / bn : rn;
+    info->rel_residual_r0 = r0 > 0 ? rn / r0 : rn;
+    info->stagnated = converged ? 0 : stagnated;
+    info->converged = converged ? 1 : 0;
+    info->refine_passes = passes > 0 ? passes - 1 : 0;
+    info->warm_iters = 0;
+    info->n_groups = 0;
+    info->negative_curvature = 0;
+    info->precision_used = BAL_PREC_DF64;
+  }
+  return BAL_OK;
+}
+
+}  // namespace bal

@@ -447,17 +447,22 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   PcgScalars h{};
-  const int chunk = 16;
-  int launched = 0;
+  const int chunk = Scene::kTimedPerChunk;
+  int launched = 0, timed = 0;
   for (;;) {
     BAL_CUDA(cudaMemcpyAsync(&h, S.pcg, sizeof(h), cudaMemcpyDeviceToHost, st));
     BAL_CUDA(cudaStreamSynchronize(st));
+    BAL_TRY(kt_collect(S, timed));
+    timed = 0;
     if (h.done || launched >= max_it) break;
     const int n = std::min(chunk, max_it - launched);
     for (int k = 0; k < n; ++k) {
       k_pcg_dir_diag<T, NT><<<G, NT, 0, st>>>(A, z, p, q, S.pcg, S.partials);
       ::bal::note_launch();
+      kt_before(S, k, st);
       k_pcg_offdiag<T, NT><<<G, NT, 0, st>>>(A.O, p, q, S.pcg, S.partials, G);
+      kt_after(S, k, st);
+      ++timed;
       ::bal::note_launch();
       k_pcg_update<T, NT><<<G, NT, 0, st>>>(A, x, p, q, r, z, S.pcg, S.partials);
       ::bal::note_launch();
@@ -600,6 +605,22 @@ static bal_status true_residual(Scene& S, const double* b, const double* x, doub
   return BAL_OK;
 }
 
+bal_status residual_fp64(Scene& S, const double* b, const double* x, double* r, double* rn,
+                         double* bn, cudaStream_t st) {
+  const int64_t n3 = 3 * (int64_t)S.d.nv;
+  BAL_TRY(spmv(S, x, S.pcg_q, st));
+  k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, r);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
+  double res[2];
+  BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  *rn = sqrt(res[0]);
+  *bn = sqrt(res[1]);
+  return BAL_OK;
+}
+
 // FP32 inner PCG on the FP32 copy of H, FP64 outer residual and correction
 // (iterative refinement): r = b - H x (FP64), solve H e = r/||r|| in FP32 to
 // mixed_inner_tol, x += ||r|| e, repeat until ||r|| <= tol ||r_0||.
@@ -670,6 +691,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     info->warm_iters = 0;
     info->n_groups = 0;
     info->negative_curvature = 0;
+    info->precision_used = BAL_PREC_MIXED;
   }
   return BAL_OK;
 }
@@ -704,6 +726,14 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
   int witers = 0, ngroups = 0;
   if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART)
     BAL_TRY(warm_start(S, b, x, &witers, &ngroups, st));
+  if (S.prm.precision == BAL_PREC_DF64) {
+    BAL_TRY(pcg_df64(S, b, x, tol, max_it, info, st));
+    if (info) {
+      info->warm_iters = witers;
+      info->n_groups = ngroups;
+    }
+    return BAL_OK;
+  }
   if (S.prm.precision == BAL_PREC_MIXED) {
     BAL_TRY(pcg_mixed(S, b, x, tol, max_it, info, st));
     if (info) {
@@ -724,6 +754,7 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
     info->warm_iters = witers;
     info->n_groups = ngroups;
     info->negative_curvature = 0;
+    info->precision_used = BAL_PREC_FP64;
     double rn, bn;
     BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
     info->rel_residual = bn > 0 ? rn / bn : rn;

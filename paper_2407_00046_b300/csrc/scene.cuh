@@ -40,6 +40,7 @@ struct PcgScalars {
   int32_t it, best_it, done, stagnated, converged, max_it, window, pad;
   uint32_t counter;   // last-block counter of the fused reductions
   uint32_t counter2;
+  float alpha_hi, alpha_lo, beta_hi, beta_lo;   // alpha, beta as double-floats
 };
 
 // Plain-old-data view of the scene's fixed device arrays, passed by value to kernels.
@@ -79,6 +80,27 @@ struct Scene {
   float *D32 = nullptr, *Dinv32 = nullptr, *Lval32 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
   bool f32_valid = false;
+  // BAL_PREC_DF64 solve (ddpcg.cu). The static lower blocks in a symmetric
+  // sliced-ELL layout of 32-row slices, built on first use: per slice the
+  // row-side list (blocks L_ij of the slice's rows, k-major: entry k of the 32
+  // rows adjacent) and the column-side list (for row i the blocks L_ki with
+  // k > i, as value positions into the row-side storage plus the source row).
+  int32_t n_slices = 0;
+  bool sell_built = false;
+  Buf sell_offR, sell_offT;   // [n_slices+1] entry offsets (multiples of 32)
+  Buf sell_Rcol;              // [offR[n]] column of each row-side entry
+  Buf sell_Tpos, sell_Tsrc;   // [offT[n]] value position / source row of each column-side entry
+  Buf sell_pos;               // [nnzL] value position of each CSR slot
+  int64_t sell_zero = 0;      // value position of an all-zero block (padding)
+  // double-float values (valid after the refresh in pcg_df64): slice-major D,
+  // D^-1 ([n_slices][9][32]), the sliced lower blocks, contact blocks [nnzC][9],
+  // six vectors x r z p q b
+  Buf dd_D, dd_Dinv, dd_R, dd_C, dd_vec;
+  bool dd_valid = false;
+  // contact rows (per assembly): unique rows touched by C or C^T, their entries
+  // (2c + transposed) and source vertices in CSR form
+  int32_t n_crows = 0;
+  Buf cr_rows, cr_ptr, cr_ent, cr_src, cr_key, cr_key_alt, cr_val, cr_val_alt, cr_cnt, cr_num;
   bool assembled = false;
   bool project = true;           // PSD projection of stencil Hessians (false: adjoint)
   double* E = nullptr;           // [nt] Young's modulus (device)
@@ -116,6 +138,13 @@ struct Scene {
   double* scal = nullptr;        // [64] scalar results
   PcgScalars* pcg = nullptr;
 
+  // per-launch timing of the SpMV kernel of each PCG iteration (bal_kernel_timing)
+  static constexpr int kTimedPerChunk = 16;
+  bool ktime = false;
+  cudaEvent_t kev[2 * kTimedPerChunk] = {};
+  double kt_ms = 0;
+  int64_t kt_n = 0;
+
   // AL state of the current time step (host copy is authoritative)
   bool step_active = false;
   double sigma = 0, sigma0 = 0, dmin_prev = 0, e0 = 0;
@@ -127,6 +156,16 @@ struct Scene {
 };
 
 constexpr int kMaxPartials = 4096;
+
+// event pair k of the current chunk around the timed kernel (no-ops unless enabled)
+inline void kt_before(Scene& S, int k, cudaStream_t st) {
+  if (S.ktime) cudaEventRecord(S.kev[2 * k], st);
+}
+inline void kt_after(Scene& S, int k, cudaStream_t st) {
+  if (S.ktime) cudaEventRecord(S.kev[2 * k + 1], st);
+}
+// after the stream has synchronised: add the first n pairs to the totals
+bal_status kt_collect(Scene& S, int n);
 
 // ---- elastic.cu ---------------------------------------------------------------
 // grad (+)= inertia + elastic gradient (pinned zeroed); init=true overwrites.
@@ -190,6 +229,14 @@ bal_status compact_f64(Scene& S, const double* in, const uint8_t* flag, int64_t 
 bal_status launch_residual_norm(Scene& S, const double* b, const double* y, cudaStream_t st);
 bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_it,
                      bal_solve_info* info, cudaStream_t st);
+// x = H^{-1} b by block-Jacobi PCG with double-float recurrences (ddpcg.cu):
+// FP64 true residuals decide convergence; restarts from the true residual when
+// the recurrence and the true residual disagree.
+bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it,
+                    bal_solve_info* info, cudaStream_t st);
+// S.scal[8] = ||b - H x||^2, S.scal[9] = ||b||^2 and r = b - H x (FP64)
+bal_status residual_fp64(Scene& S, const double* b, const double* x, double* r, double* rn,
+                         double* bn, cudaStream_t st);
 
 // ---- vec.cu ----------------------------------------------------------------------
 bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y, cudaStream_t st);
