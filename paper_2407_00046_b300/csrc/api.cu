@@ -789,7 +789,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
                  &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d,
-                 &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos,
+                 &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos, &S.sell_len,
                  &S.dd_D, &S.dd_Dinv, &S.dd_R, &S.dd_C, &S.dd_vec, &S.cr_rows, &S.cr_ptr, &S.cr_ent,
                  &S.cr_src, &S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_cnt, &S.cr_num};
   for (Buf* b : bufs) buf_free(*b);

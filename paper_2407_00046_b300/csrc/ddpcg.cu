@@ -31,18 +31,22 @@ namespace {
 
 constexpr int kDdThreads = 256;
 constexpr int kDdWarps = kDdThreads / 32;
-constexpr int kDdBlocks = 8 * kNumSM;    // CTAs of the vector kernels
 constexpr double kDdRange = 1e36;        // entries beyond this stay in the FP64 solver
+// padding entries read zero blocks; spreading them over this many chunks keeps
+// every slice's padding reads on different L2 lines instead of one hot spot
+constexpr int kZeroChunks = 64;
 
 struct DDSys {
   const dd* D;            // [ns][9][32]
   const dd* Dinv;         // [ns][9][32]
   const int32_t* offR;    // [ns+1]
   const int32_t* Rcol;    // [offR[ns]]
-  const dd* R;            // sliced lower blocks (+ one zero chunk)
+  const dd* R;            // sliced lower blocks, then one chunk of zero blocks
   const int32_t* offT;    // [ns+1]
   const int32_t* Tpos;    // [offT[ns]]
   const int32_t* Tsrc;    // [offT[ns]]
+  const short2* len;      // [ns*32] row-side and column-side list length of each row
+  int64_t zero;           // value position of the first chunk of zero blocks
   int nv, ns;
 };
 
@@ -222,7 +226,9 @@ __global__ void __launch_bounds__(NT) k_dd_dir(int nv, const dd* __restrict__ z,
 }
 
 // q = (D + L + L^T) p, one warp per slice; partial sums of p^T q. With
-// finalize, the last CTA sets alpha = rz / p^T q (no contact blocks).
+// finalize, the last CTA sets alpha = rz / p^T q (no contact blocks). Padding
+// entries read L2-resident zero chunks, so every lane runs the same loads
+// without a branch and padding costs no DRAM traffic.
 __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __restrict__ p,
                                                         dd* __restrict__ q, PcgScalars* P,
                                                         double* partials, int finalize) {
@@ -234,10 +240,16 @@ __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __res
     const bool own = i < A.nv;
     const dd3 pi = own ? dd3_ld(p, i) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
     dd3 acc = mv_sliced(A.D + slice_base(i), pi);
-    const int r1 = A.offR[s + 1];
+    // lanes past their own row-side list length (padding) read a zero chunk,
+    // which stays in L2; the column-side padding entries already point at one
+    const int lr = A.len[i].x;
+    const int r0 = A.offR[s], r1 = A.offR[s + 1];
 #pragma unroll 2
-    for (int idx = A.offR[s] + lane; idx < r1; idx += 32)
-      dd3_acc(acc, mv_sliced(A.R + 9 * (int64_t)(idx - lane) + lane, dd3_ld(p, A.Rcol[idx])));
+    for (int idx = r0 + lane; idx < r1; idx += 32) {
+      const int64_t vb = idx - r0 < 32 * lr ? 9 * (int64_t)(idx - lane) + lane
+                                            : A.zero + 288 * (s % kZeroChunks) + lane;
+      dd3_acc(acc, mv_sliced(A.R + vb, dd3_ld(p, A.Rcol[idx])));
+    }
     const int t1 = A.offT[s + 1];
 #pragma unroll 2
     for (int idx = A.offT[s] + lane; idx < t1; idx += 32)
@@ -387,7 +399,7 @@ bal_status build_sell(Scene& S) {
       lr = std::max(lr, rp[i + 1] - rp[i]);
       lt = std::max(lt, cp[i + 1] - cp[i]);
     }
-    if ((int64_t)offR[s] + 32 * (int64_t)lr > (INT32_MAX / 9 - 64) ||
+    if ((int64_t)offR[s] + 32 * (int64_t)lr > (INT32_MAX / 9 - 32 * kZeroChunks) ||
         (int64_t)offT[s] + 32 * (int64_t)lt > INT32_MAX) {
       set_error("df64 pcg: sliced storage exceeds 32-bit positions");
       return BAL_ERR_CAPACITY;
@@ -396,7 +408,7 @@ bal_status build_sell(Scene& S) {
     offT[s + 1] = offT[s] + 32 * lt;
   }
   const int64_t nR = offR[ns], nT = offT[ns];
-  const int32_t zero = 9 * (int32_t)nR;   // the zero chunk after the row-side chunks
+  const int32_t zero = 9 * (int32_t)nR;   // kZeroChunks chunks of zero blocks after the row-side chunks
   std::vector<int32_t> Rcol(nR > 0 ? nR : 1), pos(nL > 0 ? nL : 1), Tpos(nT > 0 ? nT : 1), Tsrc(nT > 0 ? nT : 1);
   // row side first: the column side refers to the value positions of later rows
   for (int s = 0; s < ns; ++s) {
@@ -411,7 +423,7 @@ bal_status build_sell(Scene& S) {
           Rcol[idx] = col[slot];
           pos[slot] = 9 * (idx - l) + l;
         } else {
-          Rcol[idx] = i < nv ? i : 0;   // a zero block times a valid entry
+          Rcol[idx] = i < nv ? i : 0;   // padding: a zero block times a valid entry
         }
       }
     }
@@ -427,12 +439,23 @@ bal_status build_sell(Scene& S) {
           Tpos[idx] = pos[cslot[cp[i] + k]];
           Tsrc[idx] = crow[cp[i] + k];
         } else {
-          Tpos[idx] = zero + l;
+          Tpos[idx] = zero + 288 * (s % kZeroChunks) + l;   // padding: a zero chunk
           Tsrc[idx] = i < nv ? i : 0;
         }
       }
     }
   }
+  std::vector<short2> len((size_t)ns * 32, short2{0, 0});
+  for (int i = 0; i < nv; ++i) {
+    const int a = rp[i + 1] - rp[i], b = cp[i + 1] - cp[i];
+    if (a > 32767 || b > 32767) {
+      set_error("df64 pcg: vertex %d has more than 32767 neighbours", i);
+      return BAL_ERR_CAPACITY;
+    }
+    len[i] = short2{(short)a, (short)b};
+  }
+  BAL_TRY(buf_reserve(S.sell_len, sizeof(short2) * len.size()));
+  BAL_CUDA(cudaMemcpy(S.sell_len.p, len.data(), sizeof(short2) * len.size(), cudaMemcpyHostToDevice));
   auto up = [&](Buf& b, const std::vector<int32_t>& v) -> bal_status {
     BAL_TRY(buf_reserve(b, sizeof(int32_t) * v.size()));
     BAL_CUDA(cudaMemcpy(b.p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
@@ -444,7 +467,7 @@ bal_status build_sell(Scene& S) {
   BAL_TRY(up(S.sell_Tpos, Tpos));
   BAL_TRY(up(S.sell_Tsrc, Tsrc));
   BAL_TRY(up(S.sell_pos, pos));
-  const size_t nRval = 9 * (size_t)(nR + 32), nDval = (size_t)ns * 9 * 32;
+  const size_t nRval = 9 * (size_t)(nR + 32 * kZeroChunks), nDval = (size_t)ns * 9 * 32;
   BAL_TRY(buf_reserve(S.dd_R, sizeof(dd) * nRval));
   BAL_TRY(buf_reserve(S.dd_D, sizeof(dd) * nDval));
   BAL_TRY(buf_reserve(S.dd_Dinv, sizeof(dd) * nDval));
@@ -548,6 +571,8 @@ DDSys dd_sys(Scene& S) {
   A.offT = S.sell_offT.as<int32_t>();
   A.Tpos = S.sell_Tpos.as<int32_t>();
   A.Tsrc = S.sell_Tsrc.as<int32_t>();
+  A.len = S.sell_len.as<short2>();
+  A.zero = S.sell_zero;
   A.nv = S.d.nv;
   A.ns = S.n_slices;
   return A;
@@ -590,6 +615,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
   dd* V = S.dd_vec.as<dd>();
   dd *ex = V, *er = V + n3, *ez = V + 2 * n3, *ep = V + 3 * n3, *eq = V + 4 * n3;
   const int gs = std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
+  const int gv = std::min((nv + kDdThreads - 1) / kDdThreads, kMaxPartials / 2);   // one vertex per thread
   const int gc = std::max(1, std::min((Cr.n + kDdThreads - 1) / kDdThreads, kMaxPartials / 2));
   const bool has_c = Cr.n > 0;
   double rn, bn;
@@ -603,7 +629,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
     init.max_it = max_it - total;
     init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
     BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-    k_dd_init<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(A, S.pcg_r, 1.0 / rn, ex, er, ez, S.pcg,
+    k_dd_init<kDdThreads><<<gv, kDdThreads, 0, st>>>(A, S.pcg_r, 1.0 / rn, ex, er, ez, S.pcg,
                                                             S.partials, tol * r0 / rn);
     ::bal::note_launch();
     BAL_LAUNCH_CHECK();
@@ -618,7 +644,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
       if (h.done || launched >= init.max_it) break;
       const int n = std::min(chunk, init.max_it - launched);
       for (int k = 0; k < n; ++k) {
-        k_dd_dir<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(nv, ez, ep, S.pcg);
+        k_dd_dir<kDdThreads><<<gv, kDdThreads, 0, st>>>(nv, ez, ep, S.pcg);
         ::bal::note_launch();
         kt_before(S, k, st);
         k_dd_spmv<<<gs, kDdThreads, 0, st>>>(A, ep, eq, S.pcg, S.partials, has_c ? 0 : 1);
@@ -629,7 +655,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
           k_dd_contact<kDdThreads><<<gc, kDdThreads, 0, st>>>(Cr, ep, eq, S.pcg, S.partials, gs);
           ::bal::note_launch();
         }
-        k_dd_update<kDdThreads><<<kDdBlocks, kDdThreads, 0, st>>>(A, ex, ep, eq, er, ez, S.pcg, S.partials);
+        k_dd_update<kDdThreads><<<gv, kDdThreads, 0, st>>>(A, ex, ep, eq, er, ez, S.pcg, S.partials);
         ::bal::note_launch();
       }
       BAL_LAUNCH_CHECK();

@@ -84,14 +84,16 @@ struct Scene {
   // sliced-ELL layout of 32-row slices, built on first use: per slice the
   // row-side list (blocks L_ij of the slice's rows, k-major: entry k of the 32
   // rows adjacent) and the column-side list (for row i the blocks L_ki with
-  // k > i, as value positions into the row-side storage plus the source row).
+  // k > i, as value positions into the row-side storage plus the source row);
+  // padding entries point at zero blocks.
   int32_t n_slices = 0;
   bool sell_built = false;
   Buf sell_offR, sell_offT;   // [n_slices+1] entry offsets (multiples of 32)
   Buf sell_Rcol;              // [offR[n]] column of each row-side entry
   Buf sell_Tpos, sell_Tsrc;   // [offT[n]] value position / source row of each column-side entry
   Buf sell_pos;               // [nnzL] value position of each CSR slot
-  int64_t sell_zero = 0;      // value position of an all-zero block (padding)
+  Buf sell_len;               // [n_slices*32] short2: row-side, column-side list length per row
+  int64_t sell_zero = 0;      // value position of the chunk of zero blocks (padding)
   // double-float values (valid after the refresh in pcg_df64): slice-major D,
   // D^-1 ([n_slices][9][32]), the sliced lower blocks, contact blocks [nnzC][9],
   // six vectors x r z p q b
