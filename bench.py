@@ -270,6 +270,7 @@ def run_ours(args, rank, world):
     pi = S.pcg_solve(rhs, sol, 0.0, 200)
     torch.cuda.synchronize()
     pcg_only = pi["iters"] / (time.perf_counter() - p0)
+    forms = precision_forms(S, sc, dev, args) if not args.no_forms else None
 
     # max over ranks
     vals = torch.tensor([ms, e2e_ms, float(pcg_iters), float(e2e_iters)], dtype=torch.float64)
@@ -323,9 +324,46 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "status": [t["status"] for t in timed],
     }
+    if forms is not None:
+        line["precision_forms"] = forms
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, nv, nnzL, nnzC)
     return line
+
+
+def precision_forms(S, sc, dev, args):
+    """The three solver precisions on the same system -- the first Newton
+    system of the workload's first step (x = x_0, no contact; the 1 GPa links
+    make it the stiff part, kappa ~ 1e8) -- solved from zero to the bench
+    tolerance: iterations, time, FP64 relative residual and the relative
+    difference of the solution to the FP64 one."""
+    import torch
+    keep = S.get_params()
+    x0 = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
+    v0 = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
+    S.step_begin(x0, v0)
+    g = torch.empty_like(x0)
+    S.assemble_hessian(x0, g)
+    b = -g.view(-1)
+    out, ref = {}, None
+    for name in ("fp64", "df64", "mixed"):
+        S.set_params(precision=PRECISIONS[name], pcg_stall_window=args.pcg_stall, mixed_inner_max=200,
+                     mixed_max_refine=40, mixed_inner_tol=1e-3)
+        sol = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = S.pcg_solve(b, sol, args.pcg_tol, 30000)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        if ref is None:
+            ref = sol.clone()
+        diff = float((sol - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
+        out[name] = {"iters": info["iters"], "seconds": round(sec, 3), "converged": info["converged"],
+                     "rel_residual": info["rel_residual"], "refine_passes": info["refine_passes"],
+                     "max_rel_diff_vs_fp64": diff, "precision_used": info["precision_used"]}
+    S.set_params(keep)
+    out["system"] = "first Newton system of step 1 (x = x_0), rhs = -gradient, x from 0"
+    return out
 
 
 def cpu_baseline(args, nv_full, nnzL_full, nnzC_full, budget_s=15.0):
@@ -404,12 +442,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scene", default="chain_net_shells")
-    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS))
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
     ap.add_argument("--newton-max", type=int, default=20,
                     help="Newton iterations per time step (cap; the step reports convergence)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
     ap.add_argument("--pcg-stall", type=int, default=5000,
                     help="PCG stagnation window (App. B uses 100; see DESIGN.md)")
     ap.add_argument("--mode", default="step", choices=["step", "pcg"],
