@@ -106,19 +106,19 @@ DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 
 def spmv_kernel_bytes(precision, nv, nnzL, nnzC):
-    """Name and algorithmic bytes of one launch of the timed SpMV kernel of a
-    PCG iteration (every stored value, index and vector entry moved once).
+    """Name and algorithmic bytes of one timed SpMV of a PCG iteration.
 
-    fp64 / mixed: the off-diagonal product (k_pcg_offdiag): lower blocks with
-    their row and column index, one read of p, q read and written once.
-    df64: the gather product (k_dd_spmv, double-floats of 8 bytes): diagonal and
-    lower blocks, the column index of the row-ordered list and the block and
-    row index of the column-ordered list, two row-pointer arrays, p read once,
-    q written once."""
+    df64 (k_dd_spmv): the method-minimal symmetric storage (Sec. 5.1) read
+    once -- diagonal and lower blocks as 8-byte double-floats, one column index
+    per block, the row pointer -- plus one read of p and one write of q. The
+    column-side index lists and the second (L2) read of each block for its
+    transpose are this kernel's overhead, not algorithmic.
+    fp64 / mixed (k_pcg_offdiag): lower blocks with their row and column index,
+    one read of p, q read and written once."""
     nb = nnzL + nnzC
     if precision == "df64":
-        ptrs = 2 * (nv + 1) * 4 * (2 if nnzC else 1)
-        return "k_dd_spmv (gather H p, double-float)", (nv + nb) * 72 + nb * 12 + ptrs + 2 * 24 * nv
+        return ("k_dd_spmv (symmetric H p, double-float gather)",
+                (nv + nb) * 72 + nb * 4 + (nv + 1) * 4 + 2 * 24 * nv)
     p = 4 if precision == "mixed" else 8
     return "k_pcg_offdiag (symmetric off-diagonal blocks, atomics)", nb * (9 * p + 8) + 3 * 3 * nv * p
 
