@@ -21,6 +21,7 @@
 // adjacent rows, and their second read is served by L2. Contact blocks are
 // added by a second kernel over the rows they touch.
 #include <cub/cub.cuh>
+#include <utility>
 
 #include "dd.cuh"
 #include "scene.cuh"
@@ -136,6 +137,14 @@ __global__ void k_crow_src(const int32_t* __restrict__ ent, const int32_t* __res
   if (blockIdx.x == 0 && threadIdx.x == 0) ptr[*nrows] = n2;
 }
 
+// Programmatic dependent launch: a PCG-loop kernel lets the next one in the
+// stream be scheduled at once, and waits for the previous grid to complete
+// (and its writes to be visible) before it reads anything that grid produced.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ inline bool dd_arrive_last(uint32_t* counter) {
   __shared__ bool last;
   __threadfence();
@@ -216,6 +225,7 @@ __global__ void __launch_bounds__(NT) k_dd_init(DDSys A, const double* __restric
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dd_dir(int nv, const dd* __restrict__ z, dd* __restrict__ p,
                                                const PcgScalars* P) {
+  pdl_enter();
   if (P->done) return;
   const bool first = P->it == 0;
   const dd beta{P->beta_hi, P->beta_lo};
@@ -232,6 +242,7 @@ __global__ void __launch_bounds__(NT) k_dd_dir(int nv, const dd* __restrict__ z,
 __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __restrict__ p,
                                                         dd* __restrict__ q, PcgScalars* P,
                                                         double* partials, int finalize) {
+  pdl_enter();
   if (P->done) return;
   const int lane = threadIdx.x & 31;
   dd pq{0.f, 0.f};
@@ -278,6 +289,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_dd_contact(DDContact Cr, const dd* __restrict__ p,
                                                    dd* __restrict__ q, PcgScalars* P, double* partials,
                                                    int n_prev) {
+  pdl_enter();
   if (P->done) return;
   dd pq{0.f, 0.f};
   for (int t = blockIdx.x * NT + threadIdx.x; t < Cr.n; t += gridDim.x * NT) {
@@ -310,6 +322,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, const dd* __restrict__ p,
                                                   const dd* __restrict__ q, dd* __restrict__ r,
                                                   dd* __restrict__ z, PcgScalars* P, double* partials) {
+  pdl_enter();
   if (P->done) return;
   const dd alpha{P->alpha_hi, P->alpha_lo};
   const dd malpha = dd_neg(alpha);
@@ -561,6 +574,22 @@ bal_status refresh_dd(Scene& S, bool* in_range, cudaStream_t st) {
   return BAL_OK;
 }
 
+// launch with programmatic stream serialisation (the kernel calls pdl_enter)
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), int grid, int block, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 DDSys dd_sys(Scene& S) {
   DDSys A;
   A.D = S.dd_D.as<dd>();
@@ -644,18 +673,26 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
       if (h.done || launched >= init.max_it) break;
       const int n = std::min(chunk, init.max_it - launched);
       for (int k = 0; k < n; ++k) {
-        k_dd_dir<kDdThreads><<<gv, kDdThreads, 0, st>>>(nv, ez, ep, S.pcg);
+        BAL_CUDA(launch_pdl(k_dd_dir<kDdThreads>, gv, kDdThreads, st, nv, (const dd*)ez, ep,
+                            (const PcgScalars*)S.pcg));
         ::bal::note_launch();
-        kt_before(S, k, st);
-        k_dd_spmv<<<gs, kDdThreads, 0, st>>>(A, ep, eq, S.pcg, S.partials, has_c ? 0 : 1);
-        kt_after(S, k, st);
-        ++timed;
+        // one SpMV per chunk is timed: an event between two launches ends
+        // their programmatic overlap
+        if (k == 0) kt_before(S, 0, st);
+        BAL_CUDA(launch_pdl(k_dd_spmv, gs, kDdThreads, st, A, (const dd*)ep, eq, S.pcg, S.partials,
+                            has_c ? 0 : 1));
+        if (k == 0) {
+          kt_after(S, 0, st);
+          ++timed;
+        }
         ::bal::note_launch();
         if (has_c) {
-          k_dd_contact<kDdThreads><<<gc, kDdThreads, 0, st>>>(Cr, ep, eq, S.pcg, S.partials, gs);
+          BAL_CUDA(launch_pdl(k_dd_contact<kDdThreads>, gc, kDdThreads, st, Cr, (const dd*)ep, eq, S.pcg,
+                              S.partials, gs));
           ::bal::note_launch();
         }
-        k_dd_update<kDdThreads><<<gv, kDdThreads, 0, st>>>(A, ex, ep, eq, er, ez, S.pcg, S.partials);
+        BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, gv, kDdThreads, st, A, ex, (const dd*)ep,
+                            (const dd*)eq, er, ez, S.pcg, S.partials));
         ::bal::note_launch();
       }
       BAL_LAUNCH_CHECK();
