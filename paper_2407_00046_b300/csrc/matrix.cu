@@ -21,6 +21,7 @@
 // for hundreds of iterations while the iterate improves) and beta. Once `done` is set the remaining launches of a chunk return at once, so
 // the host only synchronises once per chunk of iterations.
 #include <cub/cub.cuh>
+#include <utility>
 
 #include "scene.cuh"
 
@@ -196,6 +197,14 @@ __global__ void k_spmv_offdiag(OffDiag<T> O, const T* __restrict__ v, T* __restr
 }
 
 // ---- PCG ------------------------------------------------------------------------------
+// Programmatic dependent launch: a PCG-loop kernel lets the next one in the
+// stream be scheduled at once, and waits for the previous grid to complete
+// (and its writes to be visible) before it reads anything that grid produced.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // last-CTA detection for fused two-level reductions
 __device__ inline bool arrive_last(uint32_t* counter) {
   __shared__ bool last;
@@ -265,6 +274,7 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_pcg_dir_diag(Sys<T> A, const T* __restrict__ z,
                                                      T* __restrict__ p, T* __restrict__ q,
                                                      PcgScalars* P, double* partials) {
+  pdl_enter();
   if (P->done) return;
   const bool first = P->it == 0;
   const T beta = (T)P->beta;
@@ -284,6 +294,7 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag<T> O, const T* __restrict__ p,
                                                     T* __restrict__ q, PcgScalars* P,
                                                     double* partials, int n_prev) {
+  pdl_enter();
   if (P->done) return;
   const int64_t n = O.nL + O.nC;
   double plp = 0.0;
@@ -319,6 +330,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(Sys<T> A, T* __restrict__ x,
                                                    const T* __restrict__ p, const T* __restrict__ q,
                                                    T* __restrict__ r, T* __restrict__ z,
                                                    PcgScalars* P, double* partials) {
+  pdl_enter();
   if (P->done) return;
   const T alpha = (T)P->alpha;
   double rz = 0.0, rr = 0.0;
@@ -420,6 +432,22 @@ Sys<float> sys32(Scene& S) {
   return A;
 }
 
+// launch with programmatic stream serialisation (the kernel calls pdl_enter)
+template <typename... K, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(K...), int grid, int block, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T>
 bal_status spmv_t(const Sys<T>& A, const T* v, T* y, cudaStream_t st) {
   k_spmv_diag<T><<<grid_for(A.nv), kThreads, 0, st>>>(A, v, y);
@@ -457,14 +485,19 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
     if (h.done || launched >= max_it) break;
     const int n = std::min(chunk, max_it - launched);
     for (int k = 0; k < n; ++k) {
-      k_pcg_dir_diag<T, NT><<<G, NT, 0, st>>>(A, z, p, q, S.pcg, S.partials);
+      BAL_CUDA(launch_pdl(k_pcg_dir_diag<T, NT>, G, NT, st, A, (const T*)z, p, q, S.pcg, S.partials));
       ::bal::note_launch();
-      kt_before(S, k, st);
-      k_pcg_offdiag<T, NT><<<G, NT, 0, st>>>(A.O, p, q, S.pcg, S.partials, G);
-      kt_after(S, k, st);
-      ++timed;
+      // one off-diagonal product per chunk is timed: an event between two
+      // launches ends their programmatic overlap
+      if (k == 0) kt_before(S, 0, st);
+      BAL_CUDA(launch_pdl(k_pcg_offdiag<T, NT>, G, NT, st, A.O, (const T*)p, q, S.pcg, S.partials, G));
+      if (k == 0) {
+        kt_after(S, 0, st);
+        ++timed;
+      }
       ::bal::note_launch();
-      k_pcg_update<T, NT><<<G, NT, 0, st>>>(A, x, p, q, r, z, S.pcg, S.partials);
+      BAL_CUDA(launch_pdl(k_pcg_update<T, NT>, G, NT, st, A, x, (const T*)p, (const T*)q, r, z, S.pcg,
+                          S.partials));
       ::bal::note_launch();
     }
     BAL_LAUNCH_CHECK();
