@@ -102,6 +102,7 @@ FP64_PEAK_TFLOPS = 1.128
 
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
+PRECONDS = {"block-jacobi": 0, "warm-start": 1}      # bal_precond values
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 
@@ -216,7 +217,9 @@ def run_ours(args, rank, world):
     params = bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
                                 newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
                                 pcg_max_iter=30000,
-                                precision=PRECISIONS[args.precision])
+                                precision=PRECISIONS[args.precision],
+                                precond=PRECONDS[args.precond], warm_tol=args.warm_tol,
+                                warm_max_iter=args.warm_iters)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
@@ -328,7 +331,7 @@ def run_ours(args, rank, world):
             "workload": f"{sc.name}: {sc.n_tets} tets, {sc.n_verts} verts, h=1/30 s, dhat=1e-3 m",
             "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
             "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol, "pcg_stall_window": args.pcg_stall,
-            "precond": "block-Jacobi", "precision": args.precision,
+            "precond": args.precond, "precision": args.precision,
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
         },
@@ -474,6 +477,10 @@ def main():
                     help="Newton iterations per time step (cap; the step reports convergence)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
+    ap.add_argument("--precond", default="block-jacobi", choices=sorted(PRECONDS),
+                    help="block-Jacobi PCG, or preceded by the stiffness-grouped warm start (Sec. 4.2.2)")
+    ap.add_argument("--warm-tol", type=float, default=1e-2)
+    ap.add_argument("--warm-iters", type=int, default=50)
     ap.add_argument("--pcg-stall", type=int, default=5000,
                     help="PCG stagnation window (App. B uses 100; see DESIGN.md)")
     ap.add_argument("--mode", default="step", choices=["step", "pcg"],
