@@ -38,7 +38,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
-from . import barrier, contact, distance, elastic
+from . import barrier, ccd, contact, distance, elastic
 from .system import PairSet, energy_parts, gradient, hessian, inertia_target
 
 
@@ -57,6 +57,7 @@ class Params:
     contact_cap: int = 1 << 30      # Sec. 5.2 memory limit on |A|
     ca_max_iter: int = 64           # conservative-advancement iterations per pair
     freeze_al: bool = False         # hold sigma, A', mu fixed (adjoint checks)
+    step_mode: str = "ca"           # "ca": conservative advancement; "ccd": cubic CCD (Sec. 5.3)
 
 
 def sigma_floor(model):
@@ -159,7 +160,10 @@ def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
     delta = float(pnorm[sc.surf_verts].max()) if sc.surf_verts.size else 0.0
     r = model.dhat + 2.0 * delta / prm.step_bound
     cand = contact.candidate_pairs(x, sc, r)
-    alpha = step_bound(model, x, p, cand, prm)
+    if prm.step_mode == "ccd":
+        alpha = ccd.step_bound(model, x, p, cand)
+    else:
+        alpha = step_bound(model, x, p, cand, prm)
     parts_old = energy_parts(model, x, y, ps, sigma)
     E_old = sum(parts_old)
     slack = prm.ls_slack * sum(abs(t) for t in parts_old)
