@@ -80,7 +80,19 @@ typedef struct {
   int32_t ca_max_iter;        /* step bound: conservative-advancement iterations per pair (64) */
   int32_t freeze_al;          /* 1: hold sigma, A', mu fixed (no dual update, no sigma schedule,
                                  no A' rule) -- the map the adjoint differentiates */
+  int32_t step_mode;          /* bal_step_mode: line-search step bound */
+  int32_t broad_phase;        /* bal_broad_phase: candidate search */
 } bal_params;
+
+/* Step bound of the line search. CA: conservative advancement on the distance
+ * (every pair keeps (1 - step_bound) of its gap). CCD: the cubic CCD of
+ * Sec. 5.3 -- coplanarity roots by Newton-bisection with deflation, activation
+ * d_TOC < dhat + 1e-12, time of impact backtracked by 0.9 until the triple
+ * product keeps the sign of the reference frame. */
+typedef enum { BAL_STEP_CA = 0, BAL_STEP_CCD = 1 } bal_step_mode;
+/* Candidate search. GRID: uniform grid hash. LBVH: linear BVHs over triangles
+ * and edges (Sec. 5.3, broad phase). */
+typedef enum { BAL_BROAD_GRID = 0, BAL_BROAD_LBVH = 1 } bal_broad_phase;
 
 /* Scene description: HOST arrays, copied by bal_create_scene. */
 typedef struct {
@@ -253,6 +265,15 @@ BAL_API bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* so
                          void* stream);
 /* L_sigma at x with A(x) and the step's A' state (host out). */
 BAL_API bal_status bal_energy(bal_scene* scene, const double* x, double* energy_out, void* stream);
+/* Line-search step bound along x + t dir, t in [0, 1] (Sec. 5.3 / Sec. 5.2):
+ * the minimum over the given pairs (device array of pair keys, kind << 62 |
+ * first << 31 | second; kind 0 = PT (vertex, triangle), 1 = EE (edge, edge))
+ * of the conservative-advancement bound (mode BAL_STEP_CA) or of the cubic
+ * CCD's conservative time of impact (BAL_STEP_CCD), capped at 1. x and dir
+ * are device [n_verts*3] FP64; *alpha_out is host. */
+BAL_API bal_status bal_step_bound(bal_scene* scene, const double* x, const double* dir,
+                                  const uint64_t* pair_keys, int64_t n_pairs, int32_t mode,
+                                  double* alpha_out, void* stream);
 /* One Alg. 1 iteration l on x_inout (device): dual update of the previous
  * iteration, A, A' rule, gradient and convergence test, assembly, PCG, step
  * bound, backtracking line search (Sec. 5.2 memory cap). */

@@ -20,6 +20,8 @@ STATUS = {0: "OK", 1: "ARG", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "NAN", 5: "TI
           6: "CUDA", 7: "LINE_SEARCH", 8: "STATE"}
 PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
 PRECOND_BJ, PRECOND_BJ_WARMSTART = 0, 1
+STEP_CA, STEP_CCD = 0, 1
+BROAD_GRID, BROAD_LBVH = 0, 1
 
 
 class BalError(RuntimeError):
@@ -40,7 +42,7 @@ class Params(C.Structure):
                 ("warm_tol", C.c_double), ("warm_max_iter", C.c_int32),
                 ("mixed_inner_max", C.c_int32), ("mixed_inner_tol", C.c_double),
                 ("mixed_max_refine", C.c_int32), ("ca_max_iter", C.c_int32),
-                ("freeze_al", C.c_int32)]
+                ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -119,6 +121,7 @@ def load(path: str = LIB_PATH):
         "bal_set_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_get_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_kernel_timing": ([P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+        "bal_step_bound": ([P, P, P, P, C.c_int64, C.c_int32, C.POINTER(C.c_double), P], C.c_int),
         "bal_static_pattern": ([P, C.POINTER(C.c_int64), P, P], C.c_int),
         "bal_get_mass": ([P, P], C.c_int),
         "bal_step_begin": ([P, P, P, P], C.c_int),
@@ -341,6 +344,20 @@ class Scene:
         _check(load().bal_energy(self._h, _dev(x, torch.float64, 3 * self.nv), C.byref(e),
                                  _stream(stream)))
         return e.value
+
+    def step_bound(self, x, direction, keys, mode, stream=None):
+        """Line-search step bound over the pair keys (uint64 device tensor or
+        host sequence) along x + t direction: mode STEP_CA or STEP_CCD."""
+        import torch
+        n = 3 * self.nv
+        k = keys if isinstance(keys, torch.Tensor) else torch.tensor(
+            [int(v) for v in keys], dtype=torch.int64)
+        k = k.to(device="cuda", dtype=torch.int64).contiguous()
+        a = C.c_double()
+        _check(load().bal_step_bound(self._h, _dev(x, torch.float64, n), _dev(direction, torch.float64, n),
+                                     C.c_void_p(k.data_ptr()), int(k.numel()), int(mode), C.byref(a),
+                                     _stream(stream)))
+        return a.value
 
     def newton_step(self, x, stream=None):
         import torch

@@ -413,7 +413,10 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
     tb = clk::now();
     double alpha = 1.0;
     if (S.n_ls_cand > 0) {
-      BAL_TRY(launch_step_bound(S, x, S.dir, S.ls_cand.as<uint64_t>(), S.n_ls_cand, 14, st));
+      if (S.prm.step_mode == BAL_STEP_CCD)
+        BAL_TRY(launch_ccd_bound(S, x, S.dir, S.ls_cand.as<uint64_t>(), S.n_ls_cand, 14, st));
+      else
+        BAL_TRY(launch_step_bound(S, x, S.dir, S.ls_cand.as<uint64_t>(), S.n_ls_cand, 14, st));
       double ab;
       BAL_TRY(read_scalars(S, &ab, 14, 1, st));
       alpha = std::min(1.0, ab);
@@ -538,6 +541,8 @@ void bal_default_params(bal_params* p) {
   p->mixed_max_refine = 20;
   p->ca_max_iter = 64;
   p->freeze_al = 0;
+  p->step_mode = BAL_STEP_CA;
+  p->broad_phase = BAL_BROAD_GRID;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -801,6 +806,8 @@ bal_status bal_set_params(bal_scene* sc, const bal_params* p) {
   BAL_TRY(check_scene(sc));
   if (!p || !(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
       p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
+      p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
+      p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1)) {
     set_error("bal_set_params: invalid parameters");
     return BAL_ERR_ARG;
@@ -1022,6 +1029,24 @@ bal_status bal_energy(bal_scene* sc, const double* x, double* e, void* stream) {
   double P[5];
   BAL_TRY(energy_parts(S, x, S.cand.as<uint64_t>(), S.n_cand, P, st));
   *e = P[3] > 0 ? INFINITY : P[0] + P[1] + P[2];
+  return BAL_OK;
+}
+
+bal_status bal_step_bound(bal_scene* sc, const double* x, const double* dir, const uint64_t* pair_keys,
+                          int64_t n_pairs, int32_t mode, double* alpha_out, void* stream) {
+  BAL_TRY(check_scene(sc));
+  Scene& S = sc->S;
+  if (!x || !dir || !alpha_out || n_pairs < 0 || (n_pairs > 0 && !pair_keys) ||
+      (mode != BAL_STEP_CA && mode != BAL_STEP_CCD))
+    return BAL_ERR_ARG;
+  *alpha_out = 1.0;
+  if (n_pairs == 0) return BAL_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == BAL_STEP_CCD) BAL_TRY(launch_ccd_bound(S, x, dir, pair_keys, n_pairs, 14, st));
+  else BAL_TRY(launch_step_bound(S, x, dir, pair_keys, n_pairs, 14, st));
+  double ab;
+  BAL_TRY(read_scalars(S, &ab, 14, 1, st));
+  *alpha_out = std::min(1.0, ab);
   return BAL_OK;
 }
 

@@ -585,6 +585,168 @@ __global__ void __launch_bounds__(NT) k_step_bound(Dev S, const double* __restri
   if (threadIdx.x == 0) partials[blockIdx.x] = amin;
 }
 
+// ---- cubic CCD with a conservative time of impact (Sec. 5.3, narrow phase) ----
+// x(t) = x + t p; the stencil's nodes are coplanar where the triple product
+// f(t) = ((t1 - t0) x (t2 - t0)) . (p - t0) (PT) or ((a1 - a0) x (b1 - b0)) .
+// (b0 - a0) (EE) vanishes, a cubic in t. Every step is written with the
+// round-to-nearest intrinsics so that no product is contracted into an FMA.
+struct Cubic {
+  double c0, c1, c2, c3;
+};
+__device__ inline d3 add_rn(d3 a, d3 b) { return d3{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)}; }
+__device__ Cubic coplanarity_cubic(const d3 X[4], const d3 P[4], bool ee) {
+  d3 u0, u1, w0, w1, v0, v1;
+  if (ee) {
+    u0 = sub_rn(X[1], X[0]); u1 = sub_rn(P[1], P[0]);
+    w0 = sub_rn(X[3], X[2]); w1 = sub_rn(P[3], P[2]);
+    v0 = sub_rn(X[2], X[0]); v1 = sub_rn(P[2], P[0]);
+  } else {
+    u0 = sub_rn(X[2], X[1]); u1 = sub_rn(P[2], P[1]);
+    w0 = sub_rn(X[3], X[1]); w1 = sub_rn(P[3], P[1]);
+    v0 = sub_rn(X[0], X[1]); v1 = sub_rn(P[0], P[1]);
+  }
+  const d3 n0 = cross_rn(u0, w0), n1 = add_rn(cross_rn(u0, w1), cross_rn(u1, w0)), n2 = cross_rn(u1, w1);
+  return Cubic{dot_rn(n0, v0), __dadd_rn(dot_rn(n0, v1), dot_rn(n1, v0)), __dadd_rn(dot_rn(n1, v1), dot_rn(n2, v0)),
+               dot_rn(n2, v1)};
+}
+__device__ inline double cubic_at(const Cubic& c, double t) {
+  return __dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(c.c3, t), c.c2), t), c.c1), t), c.c0);
+}
+__device__ inline double cubic_slope(const Cubic& c, double t) {
+  return __dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(__dmul_rn(3.0, c.c3), t), __dmul_rn(2.0, c.c2)), t), c.c1);
+}
+// real roots of a t^2 + b t + c, ascending; returns the count (0..2)
+__device__ int quadratic_roots(double a, double b, double c, double r[2]) {
+  if (a == 0.0) {
+    if (b == 0.0) return 0;
+    r[0] = __ddiv_rn(-c, b);
+    return 1;
+  }
+  const double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(__dmul_rn(4.0, a), c));
+  if (disc < 0.0) return 0;
+  const double sq = __dsqrt_rn(disc);
+  const double q = __dmul_rn(-0.5, __dadd_rn(b, copysign(sq, b)));
+  if (q == 0.0) {
+    r[0] = __ddiv_rn(q, a);
+    return 1;
+  }
+  const double x0 = __ddiv_rn(q, a), x1 = __ddiv_rn(c, q);
+  r[0] = fmin(x0, x1);
+  r[1] = fmax(x0, x1);
+  return 2;
+}
+// root in [lo, hi], sign(f(lo)) = sign(flo) != sign(f(hi)): Newton steps kept
+// inside the bracket, bisection otherwise
+__device__ double newton_bisect(const Cubic& c, double lo, double hi, double flo) {
+  double t = __dmul_rn(0.5, __dadd_rn(lo, hi));
+  for (int it = 0; it < 200; ++it) {
+    const double ft = cubic_at(c, t);
+    if (ft == 0.0) return t;
+    if ((ft > 0) == (flo > 0)) lo = t;
+    else hi = t;
+    const double d = cubic_slope(c, t);
+    double tn = d != 0.0 ? __dsub_rn(t, __ddiv_rn(ft, d)) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+    if (!(lo < tn && tn < hi)) tn = __dmul_rn(0.5, __dadd_rn(lo, hi));
+    if (fabs(__dsub_rn(tn, t)) <= __dmul_rn(1e-15, fmax(1.0, fabs(t))) || __dsub_rn(hi, lo) <= 1e-16) return tn;
+    t = tn;
+  }
+  return t;
+}
+// coplanar times in [lo, hi], ascending (first root, then the deflated quadratic)
+__device__ int coplanar_times(const Cubic& c, double lo, double hi, double out[3]) {
+  double crit[2];
+  const int nc = quadratic_roots(__dmul_rn(3.0, c.c3), __dmul_rn(2.0, c.c2), c.c1, crit);
+  double knots[4];
+  int nk = 0;
+  knots[nk++] = lo;
+  for (int k = 0; k < nc; ++k)
+    if (lo < crit[k] && crit[k] < hi) knots[nk++] = crit[k];
+  knots[nk++] = hi;
+  double t0 = 0.0;
+  bool found = false;
+  for (int k = 0; k + 1 < nk && !found; ++k) {
+    const double fa = cubic_at(c, knots[k]), fb = cubic_at(c, knots[k + 1]);
+    if (fa == 0.0) {
+      t0 = knots[k];
+      found = true;
+    } else if ((fa > 0) != (fb > 0) || fb == 0.0) {
+      t0 = fb == 0.0 ? knots[k + 1] : newton_bisect(c, knots[k], knots[k + 1], fa);
+      found = true;
+    }
+  }
+  if (!found) return 0;
+  int n = 0;
+  out[n++] = t0;
+  const double A = c.c3, B = __dadd_rn(c.c2, __dmul_rn(A, t0)), C = __dadd_rn(c.c1, __dmul_rn(B, t0));
+  double r[2];
+  const int nr = quadratic_roots(A, B, C, r);
+  for (int k = 0; k < nr; ++k)
+    if (t0 < r[k] && r[k] <= hi) out[n++] = r[k];
+  return n;
+}
+
+// Conservative time of impact of each candidate along x + t dir (1 when the
+// pair does not activate); block minima into partials.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ccd_toi(Dev S, const double* __restrict__ x,
+                                                const double* __restrict__ dir,
+                                                const uint64_t* __restrict__ cand, int64_t nc,
+                                                double* partials) {
+  const double eps = 1e-12;
+  double amin = 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
+    int v[4];
+    d3 X[4];
+    Region R;
+    const uint64_t key = cand[i];
+    const double d0 = pair_distance(S, x, key, v, X, R);
+    d3 P[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) P[a] = ld3(dir, v[a]);
+    const bool ee = key_kind(key) != 0;
+    const Cubic c = coplanarity_cubic(X, P, ee);
+    // activation threshold: dhat + eps from outside the barrier's support, a
+    // touch (eps) for a pair already inside it
+    const double thr = d0 >= S.dhat ? __dadd_rn(eps, S.dhat) : eps;
+    double ex = 0.0, ep = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      ex = fmax(ex, fmax(fabs(__dsub_rn(X[a].x, X[0].x)), fmax(fabs(__dsub_rn(X[a].y, X[0].y)), fabs(__dsub_rn(X[a].z, X[0].z)))));
+      ep = fmax(ep, fmax(fabs(__dsub_rn(P[a].x, P[0].x)), fmax(fabs(__dsub_rn(P[a].y, P[0].y)), fabs(__dsub_rn(P[a].z, P[0].z)))));
+    }
+    const double L = __dadd_rn(ex, ep);
+    const double cmax = fmax(fmax(fabs(c.c0), fabs(c.c1)), fmax(fabs(c.c2), fabs(c.c3)));
+    if (L == 0.0 || cmax <= __dmul_rn(1e-14, __dmul_rn(__dmul_rn(L, L), L))) continue;
+    double ts[3];
+    const int nt = coplanar_times(c, -eps, __dadd_rn(1.0, eps), ts);
+    double t_prev = 0.0;
+    for (int k = 0; k < nt; ++k) {
+      const double t = ts[k];
+      d3 Xt[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        Xt[a] = d3{__dadd_rn(X[a].x, __dmul_rn(t, P[a].x)), __dadd_rn(X[a].y, __dmul_rn(t, P[a].y)),
+                   __dadd_rn(X[a].z, __dmul_rn(t, P[a].z))};
+      const Region Rt = ee ? classify_ee(Xt) : classify_pt(Xt);
+      const double d = region_distance(Xt, Rt);
+      if (d < thr) {
+        const double t_ref = __dmul_rn(0.5, __dadd_rn(fmax(t_prev, 0.0), fmax(t, 0.0)));
+        const double f_ref = cubic_at(c, t_ref);
+        double tr = fmax(t, 0.0);
+        for (int it = 0; it < 64; ++it) {
+          const double ft = cubic_at(c, tr);
+          if (ft != 0.0 && (ft > 0) == (f_ref > 0)) break;
+          tr = __dmul_rn(tr, 0.9);
+        }
+        amin = fmin(amin, fmin(1.0, tr));
+        break;
+      }
+      t_prev = t;
+    }
+  }
+  amin = block_min<double, NT>(amin, 1.0);
+  if (threadIdx.x == 0) partials[blockIdx.x] = amin;
+}
+
 // keeps a line-search candidate if it can enter A along the step (d < dhat +
 // Delta) or can constrain the step length (eta d < Delta); Delta = max |p_a - p_b|
 __global__ void k_ls_filter(Dev S, const double* __restrict__ x, const double* __restrict__ dir,
@@ -688,6 +850,16 @@ bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
   const int nblk = 2 * kNumSM;
   k_step_bound<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound,
                                         S.prm.ca_max_iter > 0 ? S.prm.ca_max_iter : 64, S.partials);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  return finish_reduce(S, nblk, slot, RED_MIN, st);
+}
+
+bal_status launch_ccd_bound(Scene& S, const double* x, const double* dir, const uint64_t* cand,
+                            int64_t ncand, int slot, cudaStream_t st) {
+  constexpr int NT = 256;
+  const int nblk = 2 * kNumSM;
+  k_ccd_toi<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.partials);
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);

@@ -197,6 +197,10 @@ bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand
 // Delta_i = max |p_a - p_b| over a node of each primitive -> S.scal[slot].
 bal_status launch_step_bound(Scene& S, const double* x, const double* dir,
                              const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st);
+// min over candidates of the conservative time of impact of the cubic CCD
+// (Sec. 5.3) along x + t dir, t in [0, 1] -> S.scal[slot].
+bal_status launch_ccd_bound(Scene& S, const double* x, const double* dir,
+                            const uint64_t* cand, int64_t ncand, int slot, cudaStream_t st);
 // flag[i] = candidate i can enter A along the step or constrain alpha
 bal_status launch_ls_filter(Scene& S, const double* x, const double* dir, const uint64_t* cand,
                             int64_t n, uint8_t* flag, cudaStream_t st);
