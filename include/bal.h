@@ -265,6 +265,16 @@ BAL_API bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* so
                          void* stream);
 /* L_sigma at x with A(x) and the step's A' state (host out). */
 BAL_API bal_status bal_energy(bal_scene* scene, const double* x, double* energy_out, void* stream);
+/* Broad phase (Sec. 5.3): the PT / EE candidate pairs (sorted keys, kind << 62
+ * | first << 31 | second) of the scene's broad_phase at x. With dir == NULL:
+ * pairs whose primitives' boxes come within r on every axis (a superset of the
+ * pairs with d < r). With dir (device [n_verts*3]): the LBVH returns the pairs
+ * whose boxes swept from x to x + dir come within r; the grid returns its
+ * line-search candidate set (r unused). keys_out: device, capacity entries;
+ * *n_out (host) is the count; BAL_ERR_CAPACITY if it exceeds capacity. */
+BAL_API bal_status bal_find_candidates(bal_scene* scene, const double* x, const double* dir, double r,
+                                       uint64_t* keys_out, int64_t capacity, int64_t* n_out,
+                                       void* stream);
 /* Line-search step bound along x + t dir, t in [0, 1] (Sec. 5.3 / Sec. 5.2):
  * the minimum over the given pairs (device array of pair keys, kind << 62 |
  * first << 31 | second; kind 0 = PT (vertex, triangle), 1 = EE (edge, edge))

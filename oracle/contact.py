@@ -122,3 +122,47 @@ def contact_terms(x, pairs, scene, inA, inAp, mu, s, sigma, dhat, project=True):
     if project:
         H = project_psd(H)
     return e, g, H, nodes, d
+
+
+def _boxes(x, idx, dirv=None):
+    """Axis-aligned boxes [n, 2, 3] of primitives idx [n, k] at x and, with dirv,
+    at x + dirv (the box swept over the step)."""
+    P = x[idx]
+    lo, hi = P.min(axis=1), P.max(axis=1)
+    if dirv is not None:
+        Q = x[idx] + dirv[idx]
+        lo, hi = np.minimum(lo, Q.min(axis=1)), np.maximum(hi, Q.max(axis=1))
+    return lo, hi
+
+
+def box_candidates(x, scene, r, dirv=None, chunk=2048):
+    """Brute force over all PT pairs (surface vertex, surface triangle not
+    containing it) and EE pairs (surface edges e < f sharing no vertex) whose
+    boxes (swept along dirv if given) come within r on every axis:
+    a.lo <= b.hi + r and b.lo <= a.hi + r. Sorted keys."""
+    sv = scene.surf_verts.astype(np.int64)
+    tris, edges = scene.tris.astype(np.int64), scene.edges.astype(np.int64)
+    vlo, vhi = _boxes(x, sv[:, None], dirv)
+    tlo, thi = _boxes(x, tris, dirv)
+    elo, ehi = _boxes(x, edges, dirv)
+    out = []
+
+    def close(alo, ahi, blo, bhi):
+        return np.all((alo[:, None, :] <= bhi[None, :, :] + r) & (blo[None, :, :] <= ahi[:, None, :] + r), axis=2)
+
+    for s in range(0, len(sv), chunk):
+        m = close(vlo[s:s + chunk], vhi[s:s + chunk], tlo, thi)
+        iv, it = np.nonzero(m)
+        v = sv[s + iv]
+        keep = ~np.any(tris[it] == v[:, None], axis=1)
+        out += list(zip([0] * int(keep.sum()), v[keep].tolist(), it[keep].tolist()))
+    for s in range(0, len(edges), chunk):
+        m = close(elo[s:s + chunk], ehi[s:s + chunk], elo, ehi)
+        ie, jf = np.nonzero(m)
+        e = s + ie
+        keep = e < jf
+        e, f = e[keep], jf[keep]
+        share = np.any(edges[e][:, :, None] == edges[f][:, None, :], axis=(1, 2))
+        out += [(1, int(a), int(b)) for a, b in zip(e[~share], f[~share])]
+    out.sort()
+    return out

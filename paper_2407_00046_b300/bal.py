@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
         "bal_get_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_kernel_timing": ([P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
         "bal_step_bound": ([P, P, P, P, C.c_int64, C.c_int32, C.POINTER(C.c_double), P], C.c_int),
+        "bal_find_candidates": ([P, P, P, C.c_double, P, C.c_int64, C.POINTER(C.c_int64), P], C.c_int),
         "bal_static_pattern": ([P, C.POINTER(C.c_int64), P, P], C.c_int),
         "bal_get_mass": ([P, P], C.c_int),
         "bal_step_begin": ([P, P, P, P], C.c_int),
@@ -344,6 +345,19 @@ class Scene:
         _check(load().bal_energy(self._h, _dev(x, torch.float64, 3 * self.nv), C.byref(e),
                                  _stream(stream)))
         return e.value
+
+    def find_candidates(self, x, r, direction=None, capacity=1 << 22, stream=None):
+        """Broad-phase candidate pair keys (sorted int64 device tensor) at x, or
+        swept along direction."""
+        import torch
+        n3 = 3 * self.nv
+        out = torch.empty(capacity, dtype=torch.int64, device="cuda")
+        n = C.c_int64()
+        d = _dev(direction, torch.float64, n3) if direction is not None else None
+        _check(load().bal_find_candidates(self._h, _dev(x, torch.float64, n3), d, float(r),
+                                          C.c_void_p(out.data_ptr()), int(capacity), C.byref(n),
+                                          _stream(stream)))
+        return out[:n.value].clone()
 
     def step_bound(self, x, direction, keys, mode, stream=None):
         """Line-search step bound over the pair keys (uint64 device tensor or

@@ -794,6 +794,8 @@ bal_status bal_destroy_scene(bal_scene* sc) {
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
                  &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d,
+                 &S.lb_pbox, &S.lb_nbox, &S.lb_keys, &S.lb_keys_alt, &S.lb_child, &S.lb_parent,
+                 &S.lb_prim, &S.lb_arrivals, &S.lb_bounds,
                  &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos, &S.sell_len,
                  &S.dd_D, &S.dd_Dinv, &S.dd_R, &S.dd_C, &S.dd_vec, &S.cr_rows, &S.cr_ptr, &S.cr_ent,
                  &S.cr_src, &S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_cnt, &S.cr_num};
@@ -1029,6 +1031,34 @@ bal_status bal_energy(bal_scene* sc, const double* x, double* e, void* stream) {
   double P[5];
   BAL_TRY(energy_parts(S, x, S.cand.as<uint64_t>(), S.n_cand, P, st));
   *e = P[3] > 0 ? INFINITY : P[0] + P[1] + P[2];
+  return BAL_OK;
+}
+
+// candidates along x + t dir: the swept LBVH query at radius r, or the grid's
+// motion pass (whose radius is fixed by the line-search rule)
+static bal_status lbvh_or_grid_motion(Scene& S, const double* x, const double* dir, double r, int64_t* n,
+                                      cudaStream_t st) {
+  if (S.prm.broad_phase == BAL_BROAD_LBVH) return lbvh_candidates(S, x, dir, r, S.cand_alt, S.ls_cand_alt, n, st);
+  return find_candidates_motion(S, x, dir, S.cand_alt, S.ls_cand_alt, n, st);
+}
+
+bal_status bal_find_candidates(bal_scene* sc, const double* x, const double* dir, double r,
+                               uint64_t* keys_out, int64_t capacity, int64_t* n_out, void* stream) {
+  BAL_TRY(check_scene(sc));
+  Scene& S = sc->S;
+  if (!x || !n_out || !(r >= 0) || capacity < 0 || (capacity > 0 && !keys_out)) return BAL_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t n = 0;
+  if (dir) BAL_TRY(lbvh_or_grid_motion(S, x, dir, r, &n, st));
+  else BAL_TRY(find_candidates(S, x, r, S.cand_alt, S.ls_cand_alt, &n, st));
+  *n_out = n;
+  if (n > capacity) {
+    set_error("bal_find_candidates: %lld pairs exceed the capacity %lld", (long long)n, (long long)capacity);
+    return BAL_ERR_CAPACITY;
+  }
+  if (n > 0)
+    BAL_CUDA(cudaMemcpyAsync(keys_out, S.cand_alt.p, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
   return BAL_OK;
 }
 

@@ -409,6 +409,7 @@ bal_status collect(Scene& S, const double* x, Grid* passes, int npass, Buf& out,
 
 bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& alt, int64_t* n,
                            cudaStream_t st) {
+  if (S.prm.broad_phase == BAL_BROAD_LBVH) return lbvh_candidates(S, x, nullptr, r, out, alt, n, st);
   Grid G{};
   G.mode = 0;
   G.half_r = 0.5 * r;
@@ -425,6 +426,9 @@ static inline double unord(unsigned long long u) {
 
 bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, Buf& out, Buf& alt,
                                   int64_t* n, cudaStream_t st) {
+  // the LBVH form keeps the pairs whose swept boxes come within dhat: every pair
+  // that can enter A during the step, and every pair the CCD bound can activate
+  if (S.prm.broad_phase == BAL_BROAD_LBVH) return lbvh_candidates(S, x, dir, S.d.dhat, out, alt, n, st);
   const int nb = S.nbody;
   // per-body mean displacement of the step, deviation bound and AABB
   BAL_CUDA(cudaMemsetAsync(S.bmean, 0, sizeof(double) * 3 * nb, st));

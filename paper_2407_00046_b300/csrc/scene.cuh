@@ -114,6 +114,9 @@ struct Scene {
 
   // broad phase scratch
   Buf bp_cells, bp_cells_alt, bp_ids, bp_ids_alt, bp_count, bp_offs;
+  // LBVH (lbvh.cu): primitive boxes, node boxes, keys, children, parents, leaf
+  // primitives, refit arrival counters, centre bounds
+  Buf lb_pbox, lb_nbox, lb_keys, lb_keys_alt, lb_child, lb_parent, lb_prim, lb_arrivals, lb_bounds;
   Buf cand, cand_alt;            // candidates at r = dhat (sorted keys)
   int64_t n_cand = 0;
   Buf dist, dist_alt;            // per-pair distances scratch
@@ -219,6 +222,12 @@ bal_status find_candidates(Scene& S, const double* x, double r, Buf& out, Buf& a
 // deviations only, different-body pairs also by |mean|.
 bal_status find_candidates_motion(Scene& S, const double* x, const double* dir, Buf& out,
                                   Buf& alt, int64_t* n, cudaStream_t st);
+
+// ---- lbvh.cu ---------------------------------------------------------------------
+// PT / EE pairs whose (swept, if dir) primitive boxes come within r on every
+// axis, from linear BVHs over the surface triangles and edges; sorted keys.
+bal_status lbvh_candidates(Scene& S, const double* x, const double* dir, double r, Buf& out, Buf& alt,
+                           int64_t* n, cudaStream_t st);
 
 // ---- matrix.cu -----------------------------------------------------------------
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
