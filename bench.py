@@ -103,6 +103,8 @@ FP64_PEAK_TFLOPS = 1.128
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
 PRECONDS = {"block-jacobi": 0, "warm-start": 1}      # bal_precond values
+STEP_MODES = {"ca": 0, "ccd": 1}                     # bal_step_mode values
+BROAD_PHASES = {"grid": 0, "lbvh": 1}                # bal_broad_phase values
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 
@@ -219,7 +221,9 @@ def run_ours(args, rank, world):
                                 pcg_max_iter=30000,
                                 precision=PRECISIONS[args.precision],
                                 precond=PRECONDS[args.precond], warm_tol=args.warm_tol,
-                                warm_max_iter=args.warm_iters)
+                                warm_max_iter=args.warm_iters,
+                                step_mode=STEP_MODES[args.step_mode],
+                                broad_phase=BROAD_PHASES[args.broad_phase])
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
@@ -332,6 +336,7 @@ def run_ours(args, rank, world):
             "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
             "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol, "pcg_stall_window": args.pcg_stall,
             "precond": args.precond, "precision": args.precision,
+            "step_bound": args.step_mode, "broad_phase": args.broad_phase,
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
         },
@@ -479,6 +484,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
     ap.add_argument("--precond", default="block-jacobi", choices=sorted(PRECONDS),
                     help="block-Jacobi PCG, or preceded by the stiffness-grouped warm start (Sec. 4.2.2)")
+    ap.add_argument("--step-mode", default="ccd", choices=sorted(STEP_MODES),
+                    help="line-search step bound: conservative advancement or cubic CCD (Sec. 5.3)")
+    ap.add_argument("--broad-phase", default="lbvh", choices=sorted(BROAD_PHASES))
     ap.add_argument("--warm-tol", type=float, default=1e-2)
     ap.add_argument("--warm-iters", type=int, default=50)
     ap.add_argument("--pcg-stall", type=int, default=5000,

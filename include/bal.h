@@ -67,7 +67,7 @@ typedef struct {
   double sigma_growth;        /* 1.2 */
   double sigma_cap;           /* 100 (times sigma0) */
   int32_t sigma_literal_max;  /* 1 = printed max(1.2 s, 100 s0) rule */
-  double step_bound;          /* 0.9: alpha_0 <= step_bound d_i / Delta_i */
+  double step_bound;          /* 0.9: CA keeps (1 - step_bound) of each gap; CCD: margin on the TOI */
   double ls_min_alpha;        /* 1e-9 (App. B) */
   double ls_slack;            /* relative energy slack for rounding noise (1e-12) */
   int64_t contact_cap;        /* Sec. 5.2 memory limit on |A| (line-search halving) */
@@ -87,8 +87,9 @@ typedef struct {
 /* Step bound of the line search. CA: conservative advancement on the distance
  * (every pair keeps (1 - step_bound) of its gap). CCD: the cubic CCD of
  * Sec. 5.3 -- coplanarity roots by Newton-bisection with deflation, activation
- * d_TOC < dhat + 1e-12, time of impact backtracked by 0.9 until the triple
- * product keeps the sign of the reference frame. */
+ * d_TOC < dhat + 1e-12 (a touch, d_TOC < 1e-12, for a pair already within
+ * dhat), time of impact backtracked by 0.9 until the triple product keeps the
+ * sign of the reference frame, then scaled by step_bound. */
 typedef enum { BAL_STEP_CA = 0, BAL_STEP_CCD = 1 } bal_step_mode;
 /* Candidate search. GRID: uniform grid hash. LBVH: linear BVHs over triangles
  * and edges (Sec. 5.3, broad phase). */

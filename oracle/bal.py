@@ -58,6 +58,8 @@ class Params:
     ca_max_iter: int = 64           # conservative-advancement iterations per pair
     freeze_al: bool = False         # hold sigma, A', mu fixed (adjoint checks)
     step_mode: str = "ca"           # "ca": conservative advancement; "ccd": cubic CCD (Sec. 5.3)
+    broad_phase: str = "grid"       # line-search candidates: "grid" (radius rule) or "lbvh"
+                                    # (boxes swept along the step within dhat)
 
 
 def sigma_floor(model):
@@ -159,9 +161,12 @@ def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
     pnorm = np.sqrt(np.sum(p * p, axis=1))
     delta = float(pnorm[sc.surf_verts].max()) if sc.surf_verts.size else 0.0
     r = model.dhat + 2.0 * delta / prm.step_bound
-    cand = contact.candidate_pairs(x, sc, r)
+    if prm.broad_phase == "lbvh":
+        cand = contact.box_candidates(x, sc, model.dhat, p)
+    else:
+        cand = contact.candidate_pairs(x, sc, r)
     if prm.step_mode == "ccd":
-        alpha = ccd.step_bound(model, x, p, cand)
+        alpha = ccd.step_bound(model, x, p, cand, prm.step_bound)
     else:
         alpha = step_bound(model, x, p, cand, prm)
     parts_old = energy_parts(model, x, y, ps, sigma)

@@ -34,7 +34,10 @@ identically (all coefficients below 1e-14 L^3, L the stencil's extent plus
 its motion) never crosses its plane and does not bound the step; roots are
 polished to 1e-15 relative; at most 64 backtracking factors of 0.9 are taken.
 The step bound of a line search is the minimum over the candidate pairs of
-their conservative TOI, and 1 when no pair activates.
+their conservative TOI scaled by the line search's margin eta (0.9): the paper
+is silent on a margin, and without one a step ends at the touching time, where
+the log barrier is still finite (distances of 1e-19 m were reached); 1 when no
+pair activates.
 """
 import numpy as np
 
@@ -136,9 +139,9 @@ def coplanar_times(c, lo=-EPS, hi=1.0 + EPS):
     return [t0] + sorted(rest)
 
 
-def pair_toi(X, P, is_ee, dhat):
-    """Conservative time of impact of one stencil (X, P [4, 3]); 1.0 if it
-    does not activate within [0, 1]."""
+def pair_toi(X, P, is_ee, dhat, eta=1.0):
+    """Conservative time of impact of one stencil (X, P [4, 3]) times eta; 1.0
+    if it does not activate within [0, 1]."""
     c = cubic_coefficients(X[None], P[None], is_ee)[0]
     L = float(np.max(np.abs(X - X[0])) + np.max(np.abs(P - P[0])))
     if L == 0.0 or np.max(np.abs(c)) <= 1e-14 * (L * L * L):
@@ -160,17 +163,18 @@ def pair_toi(X, P, is_ee, dhat):
                 if ft != 0.0 and (ft > 0) == (f_ref > 0):
                     break
                 tr *= BACKTRACK
-            return min(1.0, tr)
+            return min(1.0, eta * tr)
         t_prev = t
     return 1.0
 
 
-def step_bound(model, x, p, pairs):
-    """Minimum conservative TOI over the candidate pairs along x + t p."""
+def step_bound(model, x, p, pairs, eta=0.9):
+    """Minimum over the candidate pairs along x + t p of eta times their
+    conservative TOI (1 for pairs that do not activate)."""
     if not pairs:
         return 1.0
     sc = model.scene
     nodes = contact.stencil_nodes(pairs, sc)
     X, P = x[nodes], p[nodes]
     is_ee = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)[:, 0] == 1
-    return float(min(pair_toi(X[i], P[i], bool(is_ee[i]), model.dhat) for i in range(len(pairs))))
+    return float(min(pair_toi(X[i], P[i], bool(is_ee[i]), model.dhat, eta) for i in range(len(pairs))))

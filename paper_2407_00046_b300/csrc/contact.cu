@@ -685,13 +685,14 @@ __device__ int coplanar_times(const Cubic& c, double lo, double hi, double out[3
   return n;
 }
 
-// Conservative time of impact of each candidate along x + t dir (1 when the
-// pair does not activate); block minima into partials.
+// Conservative time of impact of each candidate along x + t dir times the
+// line-search margin (1 when the pair does not activate); block minima into
+// partials.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_ccd_toi(Dev S, const double* __restrict__ x,
                                                 const double* __restrict__ dir,
                                                 const uint64_t* __restrict__ cand, int64_t nc,
-                                                double* partials) {
+                                                double eta_margin, double* partials) {
   const double eps = 1e-12;
   double amin = 1.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
@@ -737,7 +738,7 @@ __global__ void __launch_bounds__(NT) k_ccd_toi(Dev S, const double* __restrict_
           if (ft != 0.0 && (ft > 0) == (f_ref > 0)) break;
           tr = __dmul_rn(tr, 0.9);
         }
-        amin = fmin(amin, fmin(1.0, tr));
+        amin = fmin(amin, fmin(1.0, __dmul_rn(eta_margin, tr)));
         break;
       }
       t_prev = t;
@@ -859,7 +860,7 @@ bal_status launch_ccd_bound(Scene& S, const double* x, const double* dir, const 
                             int64_t ncand, int slot, cudaStream_t st) {
   constexpr int NT = 256;
   const int nblk = 2 * kNumSM;
-  k_ccd_toi<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.partials);
+  k_ccd_toi<NT><<<nblk, NT, 0, st>>>(S.d, x, dir, cand, ncand, S.prm.step_bound, S.partials);
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   return finish_reduce(S, nblk, slot, RED_MIN, st);

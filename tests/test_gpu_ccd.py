@@ -41,7 +41,8 @@ def crossing_case():
 def test_ccd_toi_per_pair_matches_oracle(crossing_case):
     sc, m, S, x, p, cand = crossing_case
     nodes = contact.stencil_nodes(cand, sc)
-    refs = np.array([ccd.pair_toi(x[nodes[i]], p[nodes[i]], cand[i][0] == 1, m.dhat)
+    eta = bal.default_params().step_bound
+    refs = np.array([ccd.pair_toi(x[nodes[i]], p[nodes[i]], cand[i][0] == 1, m.dhat, eta)
                      for i in range(len(cand))])
     act = np.flatnonzero(refs < 1.0)
     rng = np.random.default_rng(5)
@@ -57,7 +58,7 @@ def test_ccd_toi_per_pair_matches_oracle(crossing_case):
 
 def test_ccd_step_bound_over_all_candidates(crossing_case):
     sc, m, S, x, p, cand = crossing_case
-    ref = ccd.step_bound(m, x, p, cand)
+    ref = ccd.step_bound(m, x, p, cand, bal.default_params().step_bound)
     keys = [bal.pair_key(*k) for k in cand]
     got = S.step_bound(T(x).view(-1), T(p).view(-1), keys, bal.STEP_CCD)
     assert ref < 1.0

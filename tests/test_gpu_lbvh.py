@@ -70,15 +70,18 @@ def test_grid_and_lbvh_contain_every_close_pair():
         assert close <= set(_gpu(S, x, r))
 
 
-def test_time_step_with_lbvh_and_ccd_matches_oracle():
+@pytest.mark.parametrize("mode", ["ccd", "ca"])
+def test_time_step_with_lbvh_matches_oracle(mode):
     sc = close_cubes(n=2, gap=5e-4)
     S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12, pcg_max_iter=20000,
-                                         step_mode=bal.STEP_CCD, broad_phase=bal.BROAD_LBVH))
+                                         step_mode=bal.STEP_CCD if mode == "ccd" else bal.STEP_CA,
+                                         broad_phase=bal.BROAD_LBVH))
     m = system.make_model(sc)
     x, v = T(sc.X), T(sc.V0)
     xo, vo = sc.X.copy(), sc.V0.copy()
     for _ in range(2):
         info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8, step_mode="ccd"))
+        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8, step_mode=mode,
+                                                           broad_phase="lbvh"))
         assert info["converged"] == 1
         assert np.abs(x.cpu().numpy() - xo).max() < 1e-8

@@ -26,6 +26,17 @@ def test_vertex_falling_through_triangle_hits_at_half_step():
     assert np.sign(ccd._poly(f, toi)) == np.sign(ccd._poly(f, 0.0))
 
 
+def test_step_bound_applies_the_margin_to_activated_pairs_only():
+    X = _pt([0.2, 0.1, 0.2], *TRI)
+    P = np.zeros((4, 3))
+    P[0] = [0.0, -0.2, 0.0]
+    raw = ccd.pair_toi(X, P, False, DHAT)
+    assert ccd.pair_toi(X, P, False, DHAT, eta=0.9) == pytest.approx(0.9 * raw, rel=1e-15)
+    Q = P.copy()
+    Q[0] = [0.3, 0.0, 0.0]                       # parallel motion: no activation, no margin
+    assert ccd.pair_toi(X, Q, False, DHAT, eta=0.9) == 1.0
+
+
 def test_vertex_passing_beside_triangle_does_not_activate():
     X = _pt([2.0, 0.1, 2.0], *TRI)               # crosses the plane far outside the triangle
     P = np.zeros((4, 3))
