@@ -176,6 +176,7 @@ def run_pcg_only(args):
     sc = scenes.scene_by_name(args.scene)
     params = bal.default_params(pcg_stall_window=1 << 30,
                                 precision=PRECISIONS[args.precision],
+                                broad_phase=BROAD_PHASES[args.broad_phase],
                                 mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
