@@ -105,6 +105,8 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
 PRECONDS = {"block-jacobi": 0, "warm-start": 1}      # bal_precond values
 STEP_MODES = {"ca": 0, "ccd": 1}                     # bal_step_mode values
 BROAD_PHASES = {"grid": 0, "lbvh": 1}                # bal_broad_phase values
+AL_MODES = {"algorithm1": 0, "plain": 1}             # bal_al_mode values
+PCG_TOL_MODES = {"fixed": 0, "truncated-newton": 1}  # bal_pcg_tol_mode values
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 
@@ -224,7 +226,9 @@ def run_ours(args, rank, world):
                                 precond=PRECONDS[args.precond], warm_tol=args.warm_tol,
                                 warm_max_iter=args.warm_iters,
                                 step_mode=STEP_MODES[args.step_mode],
-                                broad_phase=BROAD_PHASES[args.broad_phase])
+                                broad_phase=BROAD_PHASES[args.broad_phase],
+                                al_mode=AL_MODES[args.al_mode],
+                                pcg_tol_mode=PCG_TOL_MODES[args.pcg_tol_mode])
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
@@ -338,6 +342,7 @@ def run_ours(args, rank, world):
             "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol, "pcg_stall_window": args.pcg_stall,
             "precond": args.precond, "precision": args.precision,
             "step_bound": args.step_mode, "broad_phase": args.broad_phase,
+            "al_mode": args.al_mode, "pcg_tol_mode": args.pcg_tol_mode,
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
         },
@@ -488,6 +493,10 @@ def main():
     ap.add_argument("--step-mode", default="ccd", choices=sorted(STEP_MODES),
                     help="line-search step bound: conservative advancement or cubic CCD (Sec. 5.3)")
     ap.add_argument("--broad-phase", default="lbvh", choices=sorted(BROAD_PHASES))
+    ap.add_argument("--al-mode", default="algorithm1", choices=sorted(AL_MODES),
+                    help="Algorithm 1, or the plain inexact Newton ablation (sigma = sigma0, no A')")
+    ap.add_argument("--pcg-tol-mode", default="fixed", choices=sorted(PCG_TOL_MODES),
+                    help="fixed --pcg-tol, or App. B criterion (i) min(0.5, sqrt(||e||))")
     ap.add_argument("--warm-tol", type=float, default=1e-2)
     ap.add_argument("--warm-iters", type=int, default=50)
     ap.add_argument("--pcg-stall", type=int, default=5000,

@@ -82,7 +82,17 @@ typedef struct {
                                  no A' rule) -- the map the adjoint differentiates */
   int32_t step_mode;          /* bal_step_mode: line-search step bound */
   int32_t broad_phase;        /* bal_broad_phase: candidate search */
+  int32_t al_mode;            /* bal_al_mode: Algorithm 1, or the plain inexact Newton ablation */
+  int32_t pcg_tol_mode;       /* bal_pcg_tol_mode: per-solve PCG tolerance rule */
 } bal_params;
+
+/* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain
+ * inexact Newton method the paper ablates against -- the barrier with sigma
+ * held at sigma0, A' empty, no dual update. */
+typedef enum { BAL_AL_ALGORITHM1 = 0, BAL_AL_PLAIN = 1 } bal_al_mode;
+/* FIXED: ||r|| <= pcg_tol ||r_0|| on every solve. TRUNCATED_NEWTON: App. B
+ * criterion (i), ||r|| <= min(0.5, sqrt(||e||)) ||e|| with e the gradient. */
+typedef enum { BAL_PCG_TOL_FIXED = 0, BAL_PCG_TOL_TRUNCATED_NEWTON = 1 } bal_pcg_tol_mode;
 
 /* Step bound of the line search. CA: conservative advancement on the distance
  * (every pair keeps (1 - step_bound) of its gap). CCD: the cubic CCD of

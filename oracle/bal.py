@@ -58,6 +58,7 @@ class Params:
     ca_max_iter: int = 64           # conservative-advancement iterations per pair
     freeze_al: bool = False         # hold sigma, A', mu fixed (adjoint checks)
     step_mode: str = "ca"           # "ca": conservative advancement; "ccd": cubic CCD (Sec. 5.3)
+    al_mode: str = "bal"            # "bal": Algorithm 1; "plain": barrier with sigma = sigma0, A' empty
     broad_phase: str = "grid"       # line-search candidates: "grid" (radius rule) or "lbvh"
                                     # (boxes swept along the step within dhat)
 
@@ -240,7 +241,8 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
             sigma = sigma0
             sigma0_pending = False
             info["sigma0"] = sigma0
-        if l > 0 and frozen is None:
+        plain = prm.al_mode == "plain"   # ablation: the plain inexact Newton method
+        if l > 0 and frozen is None and not plain:
             # dual update of the previous iteration, evaluated at x^[l]
             if Ap:
                 keys = sorted(Ap)
@@ -255,7 +257,9 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
                 else:
                     sigma = min(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
         # augmentation set rule (Alg. 1 lines 3-6)
-        if frozen is not None:
+        if plain:
+            Ap = {}
+        elif frozen is not None:
             pass
         elif dmin > prm.ap_ratio * dh:
             Ap = {}

@@ -22,6 +22,8 @@ PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
 PRECOND_BJ, PRECOND_BJ_WARMSTART = 0, 1
 STEP_CA, STEP_CCD = 0, 1
 BROAD_GRID, BROAD_LBVH = 0, 1
+AL_ALGORITHM1, AL_PLAIN = 0, 1
+PCG_TOL_FIXED, PCG_TOL_TRUNCATED_NEWTON = 0, 1
 
 
 class BalError(RuntimeError):
@@ -42,7 +44,8 @@ class Params(C.Structure):
                 ("warm_tol", C.c_double), ("warm_max_iter", C.c_int32),
                 ("mixed_inner_max", C.c_int32), ("mixed_inner_tol", C.c_double),
                 ("mixed_max_refine", C.c_int32), ("ca_max_iter", C.c_int32),
-                ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32)]
+                ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32),
+                ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32)]
 
 
 class SceneDesc(C.Structure):

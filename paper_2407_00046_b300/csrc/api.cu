@@ -316,7 +316,8 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
     S.sigma = s0;
     S.sigma0_pending = false;
   }
-  if (S.l > 0 && !S.prm.freeze_al) {
+  const bool plain = S.prm.al_mode == BAL_AL_PLAIN;   // ablation: barrier only, sigma = sigma0
+  if (S.l > 0 && !S.prm.freeze_al && !plain) {
     // dual update of the previous iteration, evaluated at x^[l] (Alg. 1 lines 12-15)
     if (!S.ap_keys.empty()) {
       BAL_TRY(upload_ap(S, st));
@@ -333,7 +334,10 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
     }
   }
   // augmentation set rule (Alg. 1 lines 3-6); mu kept for pairs staying in A'
-  if (S.prm.freeze_al) {
+  if (plain) {
+    S.ap_keys.clear();
+    S.ap_mu.clear();
+  } else if (S.prm.freeze_al) {
     // A', mu and sigma held fixed
   } else if (dmin > thr) {
     S.ap_keys.clear();
@@ -384,7 +388,10 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   BAL_TRY(launch_axpy(S, n3, -1.0, S.grad, S.gtmp, S.gtmp, st));   // gtmp = -grad
   BAL_CUDA(cudaMemsetAsync(S.dir, 0, sizeof(double) * n3, st));
   bal_solve_info si;
-  BAL_TRY(pcg_solve(S, S.gtmp, S.dir, S.prm.pcg_tol, S.prm.pcg_max_iter, &si, st));
+  // per-solve tolerance: fixed, or App. B criterion (i) min(0.5, sqrt(||e||)) (x0 = 0, so r0 = -e)
+  const double tol = S.prm.pcg_tol_mode == BAL_PCG_TOL_TRUNCATED_NEWTON ? std::min(0.5, std::sqrt(en))
+                                                                        : S.prm.pcg_tol;
+  BAL_TRY(pcg_solve(S, S.gtmp, S.dir, tol, S.prm.pcg_max_iter, &si, st));
   I.pcg_iters = si.iters;
   I.pcg_rel_residual = si.rel_residual;
   I.ms_solve = ms_since(t0);
@@ -543,6 +550,8 @@ void bal_default_params(bal_params* p) {
   p->freeze_al = 0;
   p->step_mode = BAL_STEP_CA;
   p->broad_phase = BAL_BROAD_GRID;
+  p->al_mode = BAL_AL_ALGORITHM1;
+  p->pcg_tol_mode = BAL_PCG_TOL_FIXED;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -810,6 +819,8 @@ bal_status bal_set_params(bal_scene* sc, const bal_params* p) {
       p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
       p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
       p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
+      p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||
+      p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_TRUNCATED_NEWTON ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1)) {
     set_error("bal_set_params: invalid parameters");
     return BAL_ERR_ARG;
