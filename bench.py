@@ -211,6 +211,96 @@ def run_pcg_only(args):
             "spmv_gbs": round(byts / (kms * 1e-3) / 1e9, 1), "spmv_bytes": byts}
 
 
+def _scene_params(args, bal, **kw):
+    return bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
+                              newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
+                              pcg_max_iter=30000, precision=PRECISIONS[args.precision],
+                              precond=PRECONDS[args.precond], step_mode=STEP_MODES[args.step_mode],
+                              broad_phase=BROAD_PHASES[args.broad_phase], **kw)
+
+
+def run_adjoint(args):
+    """Gradient of a loss after --adj-steps steps (the squared distance of the
+    first body's centroid to the scene's target) with respect to per-tet E and
+    the initial velocity, through the autograd.Function: forward (time steps
+    with a checkpoint each) and backward (one adjoint solve per step) timed
+    separately. Default scene: the 105k-tet cube dropped on the 202k-tet slab."""
+    import torch
+    from paper_2407_00046_b300 import bal, build, scenes
+    from paper_2407_00046_b300.autograd import simulate
+    build.build(force=False, verbose=False)
+    dev = torch.device("cuda", 0)
+    name = args.scene if args.scene != "chain_net_shells" else "cube_on_slab"
+    sc = scenes.scene_by_name(name)
+    S = bal.Scene(sc, _scene_params(args, bal), pair_capacity=1 << 22)
+    mass = torch.tensor(S.mass(), device=dev)
+    body = torch.tensor(np.flatnonzero(sc.body == 0), device=dev)
+    target = torch.tensor(sc.info.get("target", sc.X.mean(0)), dtype=torch.float64, device=dev)
+    E = torch.tensor(sc.E, dtype=torch.float64, device=dev, requires_grad=True)
+    v0 = torch.tensor(sc.V0, dtype=torch.float64, device=dev).view(-1).requires_grad_(True)
+    x0 = torch.tensor(sc.X, dtype=torch.float64, device=dev).view(-1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = []
+    xT, vT = simulate(S, x0, v0, E, args.adj_steps, require_converged=False, stats=stats)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    m = mass[body]
+    c = (m[:, None] * xT.view(-1, 3)[body]).sum(0) / m.sum()
+    J = ((c - target) ** 2).sum()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"mode": "adjoint", "scene": name, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
+            "steps": args.adj_steps, "precision_forward": args.precision,
+            "forward_ms_per_step": round(1e3 * (t1 - t0) / args.adj_steps, 1),
+            "backward_ms_per_step": round(1e3 * (t2 - t1) / args.adj_steps, 1),
+            "unconverged_forward_steps": stats[0]["unconverged_steps"] if stats else None,
+            "newton_cap": args.newton_max,
+            "loss": float(J), "grad_E_norm": float(E.grad.norm()), "grad_v0_norm": float(v0.grad.norm()),
+            "data": "synthetic (seeded procedural scene)"}
+
+
+def run_precision_sweep(args):
+    """The same --steps time steps from the scene's initial state in each
+    solver precision: ms per step, Newton and PCG iterations, and the largest
+    vertex distance to the FP64 run. Default scene: the 1.05M-tet stack of 64
+    cubes with E log-uniform in [1e5, 1e9]."""
+    import torch
+    from paper_2407_00046_b300 import bal, build, scenes
+    build.build(force=False, verbose=False)
+    dev = torch.device("cuda", 0)
+    name = args.scene if args.scene != "chain_net_shells" else "cube_columns"
+    sc = scenes.scene_by_name(name)
+    out, ref = {}, None
+    for prec in ("fp64", "df64", "mixed"):
+        a = argparse.Namespace(**vars(args))
+        a.precision = prec
+        S = bal.Scene(sc, _scene_params(a, bal, mixed_inner_max=200, mixed_max_refine=40,
+                                        mixed_inner_tol=1e-3), pair_capacity=1 << 22)
+        x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
+        v = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
+        infos = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(args.steps, 1)):
+            infos.append(S.time_step(x, v, check=False))
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        xs = x.cpu().numpy()
+        if ref is None:
+            ref = xs
+        out[prec] = {"ms_per_step": round(1e3 * sec / max(args.steps, 1), 1),
+                     "newton_iters": [i["newton_iters"] for i in infos],
+                     "pcg_iters": [i["pcg_iters_total"] for i in infos],
+                     "converged": [i["converged"] for i in infos],
+                     "max_vertex_diff_vs_fp64_m": float(np.abs(xs - ref).max())}
+        del S
+    return {"mode": "precision-sweep", "scene": name, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
+            "steps": args.steps, "pcg_tol": args.pcg_tol, "results": out,
+            "data": "synthetic (seeded procedural scene)"}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2407_00046_b300 import bal, build, scenes
@@ -500,17 +590,22 @@ def main():
     ap.add_argument("--warm-tol", type=float, default=1e-2)
     ap.add_argument("--warm-iters", type=int, default=50)
     ap.add_argument("--pcg-stall", type=int, default=5000,
-                    help="PCG stagnation window (App. B uses 100; see DESIGN.md)")
-    ap.add_argument("--mode", default="step", choices=["step", "pcg"],
-                    help="pcg: assemble once and time fixed-length PCG solves (profiling)")
+                    help="PCG stagnation window (App. B uses 100; at 100 the block-Jacobi solves of "
+                         "the 1 GPa net stop before their residual starts to fall)")
+    ap.add_argument("--mode", default="step", choices=["step", "pcg", "adjoint", "precision-sweep"],
+                    help="pcg: assemble once and time fixed-length PCG solves (profiling); adjoint: "
+                         "forward + backward of --adj-steps steps through the autograd.Function; "
+                         "precision-sweep: the same steps in FP64, df64 and FP32 + refinement")
+    ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--pcg-iters", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if args.mode == "pcg":
+    if args.mode in ("pcg", "adjoint", "precision-sweep"):
+        run = {"pcg": run_pcg_only, "adjoint": run_adjoint, "precision-sweep": run_precision_sweep}
         if rank == 0:
-            print(json.dumps(run_pcg_only(args)), flush=True)
+            print(json.dumps(run[args.mode](args)), flush=True)
         return
     if args.impl == "reference":
         if rank == 0:

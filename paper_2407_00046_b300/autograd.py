@@ -11,18 +11,23 @@ from . import bal as _bal
 
 class _Simulate(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, E, v0, x0, scene, steps, adj_tol):
+    def forward(ctx, E, v0, x0, scene, steps, adj_tol, require_converged=True, stats=None):
         scene.set_materials(E.detach().cpu().double().numpy())
         x = x0.detach().clone().contiguous()
         v = v0.detach().clone().contiguous()
         ckpt = []
+        ctx.unconverged = 0
         for _ in range(steps):
             xt, vt = x.clone(), v.clone()
-            info = scene.time_step(x, v)
+            info = scene.time_step(x, v, check=False)
             if not info["converged"]:
-                raise _bal.BalError(3, "time step did not converge in the differentiated run")
+                if require_converged:
+                    raise _bal.BalError(3, "time step did not converge in the differentiated run")
+                ctx.unconverged += 1   # the adjoint of that step is then approximate
             ckpt.append((xt, vt, x.clone(), scene.get_al_state()))
         ctx.scene, ctx.ckpt, ctx.nt, ctx.adj_tol = scene, ckpt, E.numel(), adj_tol
+        if stats is not None:
+            stats.append({"steps": steps, "unconverged_steps": ctx.unconverged})
         ctx.infos = []
         return x.clone(), v.clone()
 
@@ -36,10 +41,13 @@ class _Simulate(torch.autograd.Function):
         for xt, vt, xn, al in reversed(ctx.ckpt):
             gx, gv, info = S.adjoint_step(xt, vt, xn, al, gx, gv, dE, rel_tol=ctx.adj_tol)
             ctx.infos.append(info)
-        return dE, gv, gx, None, None, None
+        return dE, gv, gx, None, None, None, None, None
 
 
-def simulate(scene, x0, v0, E, steps, adj_tol=1e-12):
+def simulate(scene, x0, v0, E, steps, adj_tol=1e-12, require_converged=True, stats=None):
     """Differentiable T-step rollout: returns (x_T, v_T); gradients flow to
-    E [n_tets], v0 and x0 [n_verts*3] (CUDA float64 tensors)."""
-    return _Simulate.apply(E, v0, x0, scene, steps, adj_tol)
+    E [n_tets], v0 and x0 [n_verts*3] (CUDA float64 tensors). With
+    require_converged=False a step that ends at the Newton cap is kept and its
+    adjoint is that of an approximate minimiser; stats (a list) receives the
+    number of such steps."""
+    return _Simulate.apply(E, v0, x0, scene, steps, adj_tol, require_converged, stats)
