@@ -48,7 +48,11 @@ typedef enum {
  * ~47-bit significand) with FP64 residuals deciding convergence; falls back to
  * FP64 for a matrix with an entry beyond 1e36. */
 typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2 } bal_precision;
-typedef enum { BAL_PRECOND_BJ = 0, BAL_PRECOND_BJ_WARMSTART = 1 } bal_precond;
+/* BJ: block-Jacobi. BJ_WARMSTART: block-Jacobi after the stiffness-grouped
+ * warm start (Sec. 4.2.2). ADDITIVE: the two-level additive preconditioner the
+ * paper compares against (App. A): 3x3 diagonal-block inverses plus exact
+ * inverses of the 27x27 blocks of 9 consecutive vertices; always FP64. */
+typedef enum { BAL_PRECOND_BJ = 0, BAL_PRECOND_BJ_WARMSTART = 1, BAL_PRECOND_ADDITIVE = 2 } bal_precond;
 
 /* Solver and schedule parameters. bal_default_params follows the paper: Newton
  * tolerance 1e-4 relative (Alg. 1 / Sec. 1 footnote), PCG 1e-4 relative with a

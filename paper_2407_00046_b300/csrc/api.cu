@@ -804,7 +804,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
                  &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d,
                  &S.lb_pbox, &S.lb_nbox, &S.lb_keys, &S.lb_keys_alt, &S.lb_child, &S.lb_parent,
-                 &S.lb_prim, &S.lb_arrivals, &S.lb_bounds,
+                 &S.lb_prim, &S.lb_arrivals, &S.lb_bounds, &S.add_inv,
                  &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos, &S.sell_len,
                  &S.dd_D, &S.dd_Dinv, &S.dd_R, &S.dd_C, &S.dd_vec, &S.cr_rows, &S.cr_ptr, &S.cr_ent,
                  &S.cr_src, &S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_cnt, &S.cr_num};
@@ -817,6 +817,7 @@ bal_status bal_set_params(bal_scene* sc, const bal_params* p) {
   BAL_TRY(check_scene(sc));
   if (!p || !(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
       p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
+      p->precond < BAL_PRECOND_BJ || p->precond > BAL_PRECOND_ADDITIVE ||
       p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
       p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
       p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||

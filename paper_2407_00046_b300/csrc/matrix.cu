@@ -511,6 +511,168 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
   return BAL_OK;
 }
 
+// ---- two-level additive preconditioner (App. A, comparison only) ------------------
+// M^{-1} = D^{-1} + sum_g B_g^T (B_g H B_g^T)^{-1} B_g over groups g of
+// kAddGroup consecutive vertices (27x27 blocks), each inverse formed once per
+// assembly by Gauss-Jordan elimination (H is SPD, so no pivoting).
+constexpr int kAddGroup = 9;
+constexpr int kAddN = 3 * kAddGroup;   // 27
+constexpr int kAddWarps = 4;
+
+// one warp per group: gather B_g H B_g^T, invert in shared memory, store
+__global__ void __launch_bounds__(32 * kAddWarps) k_add_setup(Dev S, const int32_t* __restrict__ crow,
+                                                              const int32_t* __restrict__ ccol,
+                                                              const double* __restrict__ cval, int64_t nC,
+                                                              int ngroups, double* __restrict__ inv) {
+  __shared__ double Msh[kAddWarps][kAddN][kAddN + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = blockIdx.x * kAddWarps + w;
+  if (g >= ngroups) return;
+  double(*M)[kAddN + 1] = Msh[w];
+  const int v0 = g * kAddGroup, ng = min(kAddGroup, S.nv - v0);
+  for (int e = lane; e < kAddN * kAddN; e += 32) M[e / kAddN][e % kAddN] = 0.0;
+  __syncwarp();
+  for (int e = lane; e < kAddN; e += 32)
+    if (e >= 3 * ng) M[e][e] = 1.0;   // padding rows of the last group: identity
+  for (int e = lane; e < 9 * ng; e += 32) {
+    const int a = e / 9, k = e % 9;
+    M[3 * a + k / 3][3 * a + k % 3] = S.D[9 * (int64_t)(v0 + a) + k];
+  }
+  __syncwarp();
+  if (lane < ng) {   // lane = local row: static lower blocks inside the group, both ways
+    const int v = v0 + lane;
+    for (int32_t sl = S.L_row_ptr[v]; sl < S.L_row_ptr[v + 1]; ++sl) {
+      const int j = S.L_col[sl] - v0;
+      if (j < 0 || j >= ng) continue;
+      const double* B = S.Lval + 9 * (int64_t)sl;
+      for (int k = 0; k < 9; ++k) {
+        M[3 * lane + k / 3][3 * j + k % 3] = B[k];
+        M[3 * j + k % 3][3 * lane + k / 3] = B[k];
+      }
+    }
+    int lo = 0, hi = (int)nC;   // contact lower blocks of row v (sorted by row, col)
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if (crow[m] < v) lo = m + 1;
+      else hi = m;
+    }
+    for (int c = lo; c < nC && crow[c] == v; ++c) {
+      const int j = ccol[c] - v0;
+      if (j < 0 || j >= ng) continue;
+      const double* B = cval + 9 * (int64_t)c;
+      for (int k = 0; k < 9; ++k) {
+        M[3 * lane + k / 3][3 * j + k % 3] += B[k];
+        M[3 * j + k % 3][3 * lane + k / 3] += B[k];
+      }
+    }
+  }
+  __syncwarp();
+  // in-place Gauss-Jordan inversion
+  for (int k = 0; k < kAddN; ++k) {
+    const double piv = M[k][k];
+    __syncwarp();
+    if (lane < kAddN) M[k][lane] = (lane == k ? 1.0 : M[k][lane]) / piv;
+    __syncwarp();
+    for (int i = 0; i < kAddN; ++i) {
+      if (i == k) continue;
+      const double f = M[i][k];
+      __syncwarp();
+      if (lane < kAddN) M[i][lane] = (lane == k ? 0.0 : M[i][lane]) - f * M[k][lane];
+      __syncwarp();
+    }
+  }
+  for (int e = lane; e < kAddN * kAddN; e += 32)
+    inv[(int64_t)g * kAddN * kAddN + e] = M[e / kAddN][e % kAddN];
+}
+
+// x += alpha p, r -= alpha q; partial sums of r.r (at rr_partials)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_add_update(int nv, double* __restrict__ x, const double* __restrict__ p,
+                                                   const double* __restrict__ q, double* __restrict__ r,
+                                                   PcgScalars* P, double* rr_partials) {
+  if (P->done) return;
+  const double alpha = P->alpha;
+  double rr = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < 3 * nv; i += gridDim.x * NT) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  rr = block_sum<double, NT>(rr);
+  if (threadIdx.x == 0) rr_partials[blockIdx.x] = rr;
+}
+
+// z = D^{-1} r + sum_g inv_g r_g, one warp per group; partial sums of r.z.
+// init: sets rz, best and the first direction state; otherwise also sums the
+// r.r partials of k_add_update and decides convergence, stagnation and beta.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_add_apply(Dev S, int ngroups, const double* __restrict__ inv,
+                                                  const double* __restrict__ r, double* __restrict__ z,
+                                                  PcgScalars* P, double* partials, const double* rr_partials,
+                                                  int n_rr, int init) {
+  if (!init && P->done) return;
+  constexpr int W = NT / 32;
+  const int lane = threadIdx.x & 31;
+  double rz = 0.0;
+  for (int g = blockIdx.x * W + (threadIdx.x >> 5); g < ngroups; g += gridDim.x * W) {
+    const int v0 = g * kAddGroup, ng = min(kAddGroup, S.nv - v0);
+    const bool row = lane < 3 * ng;
+    const double rl = row ? r[3 * (int64_t)v0 + lane] : 0.0;
+    const double* Ig = inv + (int64_t)g * kAddN * kAddN + (row ? lane : 0) * kAddN;
+    double acc = 0.0;
+    for (int j = 0; j < kAddN; ++j) {   // every lane shuffles; rows past the group ignore the sum
+      const double rj = __shfl_sync(0xffffffffu, rl, j);
+      if (row) acc += Ig[j] * rj;
+    }
+    if (row) {
+      // block-Jacobi part of the same row
+      const int a = lane / 3, c = lane % 3;
+      const double* Di = S.Dinv + 9 * (int64_t)(v0 + a) + 3 * c;
+      const double* rv = r + 3 * (int64_t)(v0 + a);
+      acc += Di[0] * rv[0] + Di[1] * rv[1] + Di[2] * rv[2];
+      z[3 * (int64_t)v0 + lane] = acc;
+      rz += rl * acc;
+    }
+  }
+  rz = block_sum<double, NT>(rz);
+  if (threadIdx.x == 0) partials[blockIdx.x] = rz;
+  if (arrive_last(&P->counter)) {
+    const double trz = sum_partials<NT>(partials, gridDim.x);
+    const double trr = init ? 0.0 : sum_partials<NT>(rr_partials, n_rr);
+    if (threadIdx.x == 0) {
+      if (init) {
+        P->rz = trz;
+        P->best = sqrt(fmax(trz, 0.0));
+        if (!isfinite(trz)) P->done = 2;
+      } else {
+        const int it = P->it + 1;
+        const double rn = sqrt(trr);
+        const double pn = sqrt(fmax(trz, 0.0));
+        P->it = it;
+        P->rnorm = rn;
+        if (pn < P->best) {
+          P->best = pn;
+          P->best_it = it;
+        }
+        if (!isfinite(rn)) P->done = 2;
+        else if (rn <= P->tol_abs) {
+          P->done = 1;
+          P->converged = 1;
+        } else if (it - P->best_it >= P->window) {
+          P->done = 1;
+          P->stagnated = 1;
+        } else if (it >= P->max_it) {
+          P->done = 1;
+        }
+        P->beta = trz / P->rz;
+        P->rz = trz;
+      }
+      P->counter = 0;
+    }
+  }
+}
+
 }  // namespace
 
 bal_status finish_reduce_offset(Scene& S, int offset, int n, int slot, RedOp op, cudaStream_t st) {
@@ -729,6 +891,72 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
   return BAL_OK;
 }
 
+// PCG with the two-level additive preconditioner (App. A), FP64; the
+// direction, off-diagonal and scalar kernels are those of the block-Jacobi
+// solver, the update splits into the vector update and the preconditioner.
+static bal_status pcg_additive(Scene& S, const double* b, double* x, double tol, int max_it,
+                               bal_solve_info* info, cudaStream_t st) {
+  const int nv = S.d.nv;
+  const int ngroups = (nv + kAddGroup - 1) / kAddGroup;
+  BAL_TRY(buf_reserve(S.add_inv, sizeof(double) * kAddN * kAddN * (size_t)ngroups));
+  k_add_setup<<<(ngroups + kAddWarps - 1) / kAddWarps, 32 * kAddWarps, 0, st>>>(
+      S.d, S.C_row.as<int32_t>(), S.C_col.as<int32_t>(), S.C_val.as<double>(), S.nnzC, ngroups,
+      S.add_inv.as<double>());
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  constexpr int NT = kRedThreads;
+  const int G = kRedBlocks;
+  const int Ga = std::min((ngroups + NT / 32 - 1) / (NT / 32), kMaxPartials / 2);
+  double* rr_part = S.partials + kMaxPartials / 2;
+  const Sys<double> A = sys64(S);
+  BAL_TRY(spmv(S, x, S.pcg_q, st));
+  PcgScalars init{};
+  init.max_it = max_it;
+  init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
+  BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_pcg_init<double, NT><<<G, NT, 0, st>>>(A, b, S.pcg_q, S.pcg_r, S.pcg_z, S.pcg, S.partials, tol);
+  ::bal::note_launch();
+  k_add_apply<NT><<<Ga, NT, 0, st>>>(S.d, ngroups, S.add_inv.as<double>(), S.pcg_r, S.pcg_z, S.pcg,
+                                     S.partials, rr_part, G, 1);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  PcgScalars h{};
+  int launched = 0;
+  for (;;) {
+    BAL_CUDA(cudaMemcpyAsync(&h, S.pcg, sizeof(h), cudaMemcpyDeviceToHost, st));
+    BAL_CUDA(cudaStreamSynchronize(st));
+    if (h.done || launched >= max_it) break;
+    const int n = std::min(16, max_it - launched);
+    for (int k = 0; k < n; ++k) {
+      k_pcg_dir_diag<double, NT><<<G, NT, 0, st>>>(A, S.pcg_z, S.pcg_p, S.pcg_q, S.pcg, S.partials);
+      k_pcg_offdiag<double, NT><<<G, NT, 0, st>>>(A.O, S.pcg_p, S.pcg_q, S.pcg, S.partials, G);
+      k_add_update<NT><<<G, NT, 0, st>>>(nv, x, S.pcg_p, S.pcg_q, S.pcg_r, S.pcg, rr_part);
+      k_add_apply<NT><<<Ga, NT, 0, st>>>(S.d, ngroups, S.add_inv.as<double>(), S.pcg_r, S.pcg_z, S.pcg,
+                                         S.partials, rr_part, G, 0);
+      ::bal::note_launch(4);
+    }
+    BAL_LAUNCH_CHECK();
+    launched += n;
+  }
+  if (h.done == 2 || h.done == 3) {
+    set_error("additive pcg: %s at iteration %d", h.done == 2 ? "non-finite residual" : "p^T H p <= 0", h.it);
+    return BAL_ERR_NAN;
+  }
+  if (info) {
+    info->iters = h.it;
+    info->stagnated = h.stagnated;
+    info->converged = h.converged;
+    info->refine_passes = 0;
+    info->negative_curvature = 0;
+    info->precision_used = BAL_PREC_FP64;
+    double rn, bn;
+    BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
+    info->rel_residual = bn > 0 ? rn / bn : rn;
+    info->rel_residual_r0 = h.r0norm > 0 ? rn / h.r0norm : rn;
+  }
+  return BAL_OK;
+}
+
 // Stiffness-grouped warm start (Sec. 4.2.2): block-Jacobi PCG on H_dom, the
 // Hessian without the blocks that couple different stiffness groups (a masked
 // SpMV), run to warm_tol or warm_max_iter from x; its result is x.
@@ -759,6 +987,14 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
   int witers = 0, ngroups = 0;
   if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART)
     BAL_TRY(warm_start(S, b, x, &witers, &ngroups, st));
+  if (S.prm.precond == BAL_PRECOND_ADDITIVE) {   // FP64 whatever the precision setting
+    BAL_TRY(pcg_additive(S, b, x, tol, max_it, info, st));
+    if (info) {
+      info->warm_iters = 0;
+      info->n_groups = 0;
+    }
+    return BAL_OK;
+  }
   if (S.prm.precision == BAL_PREC_DF64) {
     BAL_TRY(pcg_df64(S, b, x, tol, max_it, info, st));
     if (info) {

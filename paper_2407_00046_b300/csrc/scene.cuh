@@ -80,6 +80,7 @@ struct Scene {
   float *D32 = nullptr, *Dinv32 = nullptr, *Lval32 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
   bool f32_valid = false;
+  Buf add_inv;                   // additive preconditioner: inverses of the 27x27 group blocks
   // BAL_PREC_DF64 solve (ddpcg.cu). The static lower blocks in a symmetric
   // sliced-ELL layout of 32-row slices, built on first use: per slice the
   // row-side list (blocks L_ij of the slice's rows, k-major: entry k of the 32
