@@ -102,7 +102,7 @@ FP64_PEAK_TFLOPS = 1.128
 
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
-PRECONDS = {"block-jacobi": 0, "warm-start": 1}      # bal_precond values
+PRECONDS = {"block-jacobi": 0, "warm-start": 1, "additive": 2}   # bal_precond values
 STEP_MODES = {"ca": 0, "ccd": 1}                     # bal_step_mode values
 BROAD_PHASES = {"grid": 0, "lbvh": 1}                # bal_broad_phase values
 AL_MODES = {"algorithm1": 0, "plain": 1}             # bal_al_mode values
@@ -461,7 +461,9 @@ def run_ours(args, rank, world):
 
 
 def precision_forms(S, sc, dev, args):
-    """The three solver precisions on the same system -- the first Newton
+    """The solver forms -- three precisions with block-Jacobi, and in FP64 the
+    additive (App. A) and warm-start (Sec. 4.2.2) preconditioners -- on the
+    same system: the first Newton
     system of the workload's first step (x = x_0, no contact; the 1 GPa links
     make it the stiff part, kappa ~ 1e8) -- solved from zero to the bench
     tolerance: iterations, time, FP64 relative residual and the relative
@@ -475,9 +477,13 @@ def precision_forms(S, sc, dev, args):
     S.assemble_hessian(x0, g)
     b = -g.view(-1)
     out, ref = {}, None
-    for name in ("fp64", "df64", "mixed"):
-        S.set_params(precision=PRECISIONS[name], pcg_stall_window=args.pcg_stall, mixed_inner_max=200,
-                     mixed_max_refine=40, mixed_inner_tol=1e-3)
+    forms = [("fp64", "fp64", "block-jacobi"), ("df64", "df64", "block-jacobi"),
+             ("mixed", "mixed", "block-jacobi"), ("fp64_additive", "fp64", "additive"),
+             ("fp64_warm_start", "fp64", "warm-start")]
+    for name, prec, pc in forms:
+        S.set_params(precision=PRECISIONS[prec], precond=PRECONDS[pc], pcg_stall_window=args.pcg_stall,
+                     mixed_inner_max=200, mixed_max_refine=40, mixed_inner_tol=1e-3,
+                     warm_tol=args.warm_tol, warm_max_iter=args.warm_iters)
         sol = torch.zeros_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -489,7 +495,8 @@ def precision_forms(S, sc, dev, args):
         diff = float((sol - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
         out[name] = {"iters": info["iters"], "seconds": round(sec, 3), "converged": info["converged"],
                      "rel_residual": info["rel_residual"], "refine_passes": info["refine_passes"],
-                     "max_rel_diff_vs_fp64": diff, "precision_used": info["precision_used"]}
+                     "max_rel_diff_vs_fp64": diff, "precision_used": info["precision_used"],
+                     "warm_iters": info["warm_iters"]}
     S.set_params(keep)
     out["system"] = "first Newton system of step 1 (x = x_0), rhs = -gradient, x from 0"
     return out

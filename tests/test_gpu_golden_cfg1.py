@@ -1,0 +1,35 @@
+"""The two-cube workload (two 7^3-cell Neo-Hookean cubes, 4,116 tets, 1 cm
+gap, E = 1e5, ten steps) through the C ABI against the oracle's trajectory,
+stored by tests/golden/make_cfg1_two_cubes.py (FP64 CPU, dense Cholesky
+solves): positions after every step while the oracle's steps converge."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2407_00046_b300 import bal, scenes  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "cfg1_two_cubes.npz")
+
+
+def test_cfg1_trajectory_matches_the_oracle_golden_file():
+    g = np.load(GOLD)
+    sc = scenes.two_cubes()
+    S = bal.Scene(sc, bal.default_params(newton_tol=float(g["newton_tol"]), newton_max_iter=int(g["newton_max"]),
+                                         pcg_tol=1e-12, pcg_max_iter=20000))
+    x = torch.tensor(sc.X, dtype=torch.float64, device="cuda")
+    v = torch.tensor(sc.V0, dtype=torch.float64, device="cuda")
+    compared = 0
+    for k in range(len(g["x"])):
+        info = S.time_step(x, v, check=False)
+        if not g["converged"][k]:
+            break                                # past an unconverged oracle step the states may part
+        assert info["converged"] == 1, k
+        err = np.abs(x.cpu().numpy() - g["x"][k]).max()
+        assert err < 1e-8, (k, err)
+        assert np.abs(v.cpu().numpy() - g["v"][k]).max() < 1e-8 / sc.h * 10, k
+        compared += 1
+    assert compared >= 3
