@@ -29,7 +29,12 @@ paper used here (each one is recorded in the design notes):
   dhat + 2 max|p_v| / 0.9 contains every pair that can constrain alpha or
   enter A during the step; halve until no tet is
   inverted, the number of active pairs is within the memory cap (Sec. 5.2),
-  and L_sigma does not increase by more than a rounding slack.
+  and L_sigma does not increase by more than a rounding slack;
+* friction (Sec. 4.1, chi > 0): lambda, the normal and the closest-point
+  weights of every pair of A u A' are lagged at x^[l] after the A' rule and
+  s_i are settled, held fixed through the gradient, the Hessian and the line
+  search of that iteration, and refreshed at the next one; sigma0 and the
+  dual update see no friction.
 """
 import dataclasses
 import math
@@ -38,7 +43,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
-from . import barrier, ccd, contact, distance, elastic
+from . import barrier, ccd, contact, distance, elastic, friction
 from .system import PairSet, energy_parts, gradient, hessian, inertia_target
 
 
@@ -61,6 +66,8 @@ class Params:
     al_mode: str = "bal"            # "bal": Algorithm 1; "plain": barrier with sigma = sigma0, A' empty
     broad_phase: str = "grid"       # line-search candidates: "grid" (radius rule) or "lbvh"
                                     # (boxes swept along the step within dhat)
+    friction: float = 0.0           # chi (Sec. 4.1); 0 = frictionless
+    eps_v: float = 0.0              # mollifier threshold (m/s); 0 = dhat (Table 1 caption)
 
 
 def sigma_floor(model):
@@ -157,7 +164,17 @@ def step_bound(model, x, p, pairs, prm: Params):
     return float(min(1.0, t.min()))
 
 
-def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
+def friction_set(model, x, x_t, ps: PairSet, sigma, prm: Params):
+    """Friction data of the pairs of ps lagged at x (None when chi = 0)."""
+    if prm.friction <= 0.0 or not ps.keys:
+        return None
+    d, regions, nodes = contact.pair_distances(x, ps.keys, model.scene)
+    _, e1, _ = contact.phi_derivs(d, ps.inA, ps.inAp, ps.mu, ps.s, sigma, model.dhat)
+    eps_v = prm.eps_v if prm.eps_v > 0.0 else model.dhat
+    return friction.lag(x, x_t, nodes, regions, -e1, prm.friction, eps_v * model.h)
+
+
+def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params, fric=None):
     sc = model.scene
     pnorm = np.sqrt(np.sum(p * p, axis=1))
     delta = float(pnorm[sc.surf_verts].max()) if sc.surf_verts.size else 0.0
@@ -170,7 +187,7 @@ def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
         alpha = ccd.step_bound(model, x, p, cand, prm.step_bound)
     else:
         alpha = step_bound(model, x, p, cand, prm)
-    parts_old = energy_parts(model, x, y, ps, sigma)
+    parts_old = energy_parts(model, x, y, ps, sigma, fric)
     E_old = sum(parts_old)
     slack = prm.ls_slack * sum(abs(t) for t in parts_old)
     Ap_idx = [i for i, f in enumerate(ps.inAp) if f]
@@ -197,7 +214,7 @@ def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params):
                       np.array([k in Ap_keys for k in keys], dtype=bool),
                       np.array([Ap_keys.get(k, (0.0, 0.0))[0] for k in keys]),
                       np.array([Ap_keys.get(k, (0.0, 0.0))[1] for k in keys]))
-        E_new = sum(energy_parts(model, xn, y, psn, sigma))
+        E_new = sum(energy_parts(model, xn, y, psn, sigma, fric))
         if E_new - E_old <= slack:
             return alpha, xn, dict(trials=trials, E_old=E_old, E_new=E_new,
                                    n_cand=len(cand))
@@ -267,7 +284,8 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
             Ap = {k: Ap.get(k, 0.0) for k, dd in zip(A_keys, A_d) if dd < prm.ap_ratio * dh}
         dmin_prev = dmin
         ps = make_pairset(model, x, A_keys, Ap, sigma)
-        e = gradient(model, x, y, ps, sigma)
+        fs = friction_set(model, x, x_t, ps, sigma, prm)
+        e = gradient(model, x, y, ps, sigma, fric=fs)
         en = float(np.linalg.norm(e))
         rec = dict(l=l, nA=len(A_keys), nAp=len(Ap), sigma=sigma, dmin=dmin, enorm=en)
         info["log"].append(rec)
@@ -276,9 +294,9 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
         if en <= prm.newton_abs_tol or (l > 0 and en <= prm.newton_tol * e0):
             info["converged"] = True
             break
-        H = hessian(model, x, y, ps, sigma)
+        H = hessian(model, x, y, ps, sigma, fric=fs)
         p = solve(H, -e.ravel()).reshape(-1, 3)
-        alpha, xn, lsi = line_search(model, x, y, p, ps, sigma, prm)
+        alpha, xn, lsi = line_search(model, x, y, p, ps, sigma, prm, fs)
         rec["alpha"] = alpha
         rec["ls_trials"] = lsi["trials"]
         info["iters"] = l + 1

@@ -3,7 +3,9 @@ Hessian and assembled stiffness Lambda, FP64 (test infrastructure).
 
 Incremental potential (Sec. 3.1):
     E(x) = 1/(2 h^2) ||x - y||_M^2 + Psi(x),   y = x_t + h v_t + h^2 g,
-with the lumped mass M. Friction D is zero (the workloads are frictionless).
+with the lumped mass M. The friction potential D of Sec. 4.1 (oracle/friction)
+enters every function below through the optional lagged friction set `fric`
+(None = frictionless, the default).
 BAL objective (Sec. 3.3, Eq. aug-lag):
     L_sigma(x) = E(x) + sigma sum_{i in A} b(d_i, dhat)
                + sum_{i in A'} [ mu_i (dhat + s_i - d_i) + sigma b(d_i, dhat + s_i) ].
@@ -23,7 +25,7 @@ import dataclasses
 import numpy as np
 import scipy.sparse as sp
 
-from . import contact, elastic
+from . import contact, elastic, friction
 
 
 @dataclasses.dataclass
@@ -73,9 +75,9 @@ def empty_pairs():
     return PairSet([], z.astype(bool), z.astype(bool), z, z)
 
 
-def energy_parts(model, x, y, pairs: PairSet, sigma):
+def energy_parts(model, x, y, pairs: PairSet, sigma, fric=None):
     """(inertia, elastic, contact) terms of L_sigma at x; elastic is +inf if
-    any tet is inverted."""
+    any tet is inverted. The contact term includes friction when fric is given."""
     sc = model.scene
     r = x - y
     inertia = 0.5 / model.h ** 2 * np.sum(model.mass[model.free] * np.sum(r[model.free] ** 2, axis=1))
@@ -86,11 +88,12 @@ def energy_parts(model, x, y, pairs: PairSet, sigma):
         d, _, _ = contact.pair_distances(x, pairs.keys, sc)
         e, _, _ = contact.phi_derivs(d, pairs.inA, pairs.inAp, pairs.mu, pairs.s, sigma, model.dhat)
         con = float(np.sum(e))
+    con += friction.energy(fric, x)
     return float(inertia), el, con
 
 
-def energy(model, x, y, pairs, sigma):
-    return float(sum(energy_parts(model, x, y, pairs, sigma)))
+def energy(model, x, y, pairs, sigma, fric=None):
+    return float(sum(energy_parts(model, x, y, pairs, sigma, fric)))
 
 
 def _scatter_vec(n_v, nodes, g):
@@ -100,7 +103,7 @@ def _scatter_vec(n_v, nodes, g):
     return out
 
 
-def gradient(model, x, y, pairs: PairSet, sigma, parts=False):
+def gradient(model, x, y, pairs: PairSet, sigma, parts=False, fric=None):
     """grad L_sigma [N_v,3], pinned rows zeroed. With parts=True also returns
     (inertia + elastic) gradient and the contact gradient separately."""
     sc = model.scene
@@ -114,6 +117,9 @@ def gradient(model, x, y, pairs: PairSet, sigma, parts=False):
                                                   pairs.mu, pairs.s, sigma, model.dhat,
                                                   project=False)
         gc = _scatter_vec(model.n, nodes, g)
+    if fric is not None and fric.nodes.shape[0]:
+        _, gf, _ = friction.terms(fric, x, hessian=False)
+        gc = gc + _scatter_vec(model.n, fric.nodes, gf)
     gE[~model.free] = 0.0
     gc[~model.free] = 0.0
     if parts:
@@ -130,9 +136,11 @@ def _coo_blocks(nodes, H, n_dof):
     return rows, cols, H.ravel()
 
 
-def hessian(model, x, y, pairs: PairSet, sigma, project=True, with_lambda=False):
+def hessian(model, x, y, pairs: PairSet, sigma, project=True, with_lambda=False, fric=None):
     """Assembled PSD-projected Hessian of L_sigma as scipy CSR [3N_v, 3N_v],
-    pinned rows / columns eliminated with diagonal m/h^2."""
+    pinned rows / columns eliminated with diagonal m/h^2. Friction stencils
+    (PSD by construction, not projected) add their Hessians and their trace
+    means to Lambda."""
     sc = model.scene
     nd = 3 * model.n
     _, _, He = elastic.element_terms(x, sc.tets, model.Dm_inv, model.vol, model.mu,
@@ -156,6 +164,16 @@ def hessian(model, x, y, pairs: PairSet, sigma, project=True, with_lambda=False)
         for k in range(4):
             for a in range(3):
                 np.add.at(lam, 3 * nodes[:, k] + a, tr_c)
+    if fric is not None and fric.nodes.shape[0]:
+        _, _, Hf = friction.terms(fric, x)
+        r3, c3, v3 = _coo_blocks(fric.nodes, Hf, nd)
+        rows.append(r3)
+        cols.append(c3)
+        vals.append(v3)
+        tr_f = np.trace(Hf, axis1=1, axis2=2) / 12.0
+        for k in range(4):
+            for a in range(3):
+                np.add.at(lam, 3 * fric.nodes[:, k] + a, tr_f)
     dm = np.repeat(model.mass / model.h ** 2, 3)
     rows.append(np.arange(nd))
     cols.append(np.arange(nd))

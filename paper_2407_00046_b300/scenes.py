@@ -397,6 +397,24 @@ def cube_on_slab(n_cube: int = 26, L: float = 0.1, slab_cells=(58, 10, 58),
     ], info=dict(target=target, cube_body=0, n_cube=n_cube, seed=seed))
 
 
+def sliding_cube(n_cube: int = 3, L: float = 0.05, slab_size=(0.3, 0.02, 0.3),
+                 gap: float = 5e-4, speed: float = 1.0, E: float = 1e5) -> Scene:
+    """A lattice cube resting `gap` (inside dhat) on a fully pinned one-cell
+    slab and sliding at `speed` along the slab's top diagonal (the line
+    x = z): the friction workload (Sec. 4.1). The cube's vertices stay half a
+    cell off that line, so every pair within dhat is an interior PT or EE pair
+    with a vertical normal and Coulomb's law fixes the tangential impulse per
+    step from the normal one."""
+    Xs, Ts = lattice_box(1, 1, 1, slab_size)
+    Xs = Xs - np.array([slab_size[0] / 2, slab_size[1], slab_size[2] / 2])
+    Xc, Tc = _cube(n_cube, L, lower_corner=(-0.12, gap, -0.12 - L / (2 * n_cube)))
+    v0 = speed * np.array([1.0, 0.0, 1.0]) / np.sqrt(2.0)
+    return merge_bodies("sliding_cube", [
+        dict(X=Xc, tets=Tc, E=E, V0=v0),
+        dict(X=Xs, tets=Ts, E=1e6, pinned=np.ones(Xs.shape[0], bool)),
+    ], info=dict(n_cube=n_cube, gap=gap, cube_body=0))
+
+
 def chain_net_shells(nx: int = 9, nz: int = 10, R: float = 0.035, half: float = 0.006,
                      e: float = 0.014, n_shells: int = 4, shell_radius: float = 0.10,
                      shell_thick: float = 0.01, shell_m: int = 32, shell_layers: int = 4,
@@ -470,5 +488,6 @@ def scene_by_name(name: str) -> Scene:
         "cube_on_slab": lambda: cube_on_slab(),
         "cube_on_slab_small": lambda: cube_on_slab(n_cube=4, slab_cells=(8, 2, 8)),
         "cube_columns": lambda: cube_columns(),
+        "sliding_cube": lambda: sliding_cube(),
     }
     return table[name]()
