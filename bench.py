@@ -318,7 +318,8 @@ def run_ours(args, rank, world):
                                 step_mode=STEP_MODES[args.step_mode],
                                 broad_phase=BROAD_PHASES[args.broad_phase],
                                 al_mode=AL_MODES[args.al_mode],
-                                pcg_tol_mode=PCG_TOL_MODES[args.pcg_tol_mode])
+                                pcg_tol_mode=PCG_TOL_MODES[args.pcg_tol_mode],
+                                friction=args.friction)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
@@ -433,6 +434,7 @@ def run_ours(args, rank, world):
             "precond": args.precond, "precision": args.precision,
             "step_bound": args.step_mode, "broad_phase": args.broad_phase,
             "al_mode": args.al_mode, "pcg_tol_mode": args.pcg_tol_mode,
+            "friction": args.friction,
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
         },
@@ -594,6 +596,8 @@ def main():
                     help="Algorithm 1, or the plain inexact Newton ablation (sigma = sigma0, no A')")
     ap.add_argument("--pcg-tol-mode", default="fixed", choices=sorted(PCG_TOL_MODES),
                     help="fixed --pcg-tol, or App. B criterion (i) min(0.5, sqrt(||e||))")
+    ap.add_argument("--friction", type=float, default=0.0,
+                    help="friction coefficient chi of the fully-implicit friction (0 = frictionless)")
     ap.add_argument("--warm-tol", type=float, default=1e-2)
     ap.add_argument("--warm-iters", type=int, default=50)
     ap.add_argument("--pcg-stall", type=int, default=5000,

@@ -88,6 +88,12 @@ typedef struct {
   int32_t broad_phase;        /* bal_broad_phase: candidate search */
   int32_t al_mode;            /* bal_al_mode: Algorithm 1, or the plain inexact Newton ablation */
   int32_t pcg_tol_mode;       /* bal_pcg_tol_mode: per-solve PCG tolerance rule */
+  double friction;            /* chi of Sec. 4.1 (>= 0; 0 = frictionless). Fully-implicit
+                                 friction: every pair of A u A' adds chi lambda f(|w|) with
+                                 the normal force lambda, the contact normal and the
+                                 closest-point weights lagged at each Newton iterate */
+  double friction_eps_v;      /* mollifier threshold eps_v (m/s; 0 = dhat, Table 1 caption);
+                                 the static zone is |tangent slip| < eps_v h */
 } bal_params;
 
 /* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain
@@ -343,7 +349,8 @@ BAL_API bal_status bal_set_materials(bal_scene* scene, const double* E, const do
  * lam are linear in E). If PCG finds H indefinite it falls back to the
  * projected H and sets info->negative_curvature. All vectors are DEVICE
  * [n_verts*3]; dLdE_accum is DEVICE [n_tets] (accumulated). Overwrites the
- * scene's current step state (y, A', mu, sigma). */
+ * scene's current step state (y, A', mu, sigma). Frictionless steps only:
+ * returns BAL_ERR_ARG when params.friction > 0. */
 BAL_API bal_status bal_adjoint_step(bal_scene* scene, const double* x_t, const double* v_t,
                                     const double* x_next, const bal_al_state* al,
                                     const double* dLdx_next, const double* dLdv_next,

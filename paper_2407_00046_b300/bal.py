@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("mixed_inner_max", C.c_int32), ("mixed_inner_tol", C.c_double),
                 ("mixed_max_refine", C.c_int32), ("ca_max_iter", C.c_int32),
                 ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32),
-                ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32)]
+                ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32),
+                ("friction", C.c_double), ("friction_eps_v", C.c_double)]
 
 
 class SceneDesc(C.Structure):

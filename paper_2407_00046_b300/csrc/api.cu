@@ -272,7 +272,10 @@ bal_status initial_sigma(Scene& S, const double* x, const std::vector<uint64_t>&
   S.sigma = 1.0;
   BAL_TRY(build_eval(S, x, A, st));
   BAL_CUDA(cudaMemsetAsync(S.gtmp, 0, sizeof(double) * 3 * S.d.nv, st));
-  BAL_TRY(launch_contact_terms(S, x, S.gtmp, false, st));
+  S.fric_suspend = true;   // sigma0 weighs the barrier gradient alone
+  const bal_status cs = launch_contact_terms(S, x, S.gtmp, false, st);
+  S.fric_suspend = false;
+  BAL_TRY(cs);
   S.ap_keys = keep_keys;
   S.ap_mu = keep_mu;
   S.sigma = keep_sigma;
@@ -521,6 +524,18 @@ const char* bal_last_error(void) { return g_err; }
 
 uint64_t bal_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+static bool params_ok(const bal_params* p) {
+  return p && !(!(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
+      p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
+      p->precond < BAL_PRECOND_BJ || p->precond > BAL_PRECOND_ADDITIVE ||
+      p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
+      p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
+      p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||
+      p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_TRUNCATED_NEWTON ||
+      !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
+      !(p->friction >= 0) || !(p->friction_eps_v >= 0));
+}
+
 void bal_default_params(bal_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -552,6 +567,8 @@ void bal_default_params(bal_params* p) {
   p->broad_phase = BAL_BROAD_GRID;
   p->al_mode = BAL_AL_ALGORITHM1;
   p->pcg_tol_mode = BAL_PCG_TOL_FIXED;
+  p->friction = 0.0;
+  p->friction_eps_v = 0.0;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -589,6 +606,10 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
       set_error("bal_create_scene: surface vertex index out of range");
       return BAL_ERR_ARG;
     }
+  if (params && !params_ok(params)) {
+    set_error("bal_create_scene: invalid parameters");
+    return BAL_ERR_ARG;
+  }
   bal_scene* sc = new bal_scene();
   Scene& S = sc->S;
   S.d.nv = nv;
@@ -815,14 +836,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
 
 bal_status bal_set_params(bal_scene* sc, const bal_params* p) {
   BAL_TRY(check_scene(sc));
-  if (!p || !(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
-      p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
-      p->precond < BAL_PRECOND_BJ || p->precond > BAL_PRECOND_ADDITIVE ||
-      p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
-      p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
-      p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||
-      p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_TRUNCATED_NEWTON ||
-      !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1)) {
+  if (!params_ok(p)) {
     set_error("bal_set_params: invalid parameters");
     return BAL_ERR_ARG;
   }
@@ -880,6 +894,7 @@ bal_status bal_step_begin(bal_scene* sc, const double* x_t, const double* v_t, v
   S.dmin_prev = INFINITY;
   S.l = 0;
   S.e0 = 0.0;
+  S.n_fr = 0;
   S.step_active = true;
   S.sigma0_pending = false;
   if (S.prm.freeze_al) return BAL_OK;   // keep sigma, A', mu as set by bal_set_al_state
@@ -1040,6 +1055,7 @@ bal_status bal_energy(bal_scene* sc, const double* x, double* e, void* stream) {
   std::vector<double> Ad;
   BAL_TRY(detect_active(S, x, A, Ad, st));
   BAL_TRY(build_eval(S, x, A, st));
+  if (S.prm.friction > 0.0) BAL_TRY(launch_contact_terms(S, x, nullptr, false, st));   // lag friction at x
   double P[5];
   BAL_TRY(energy_parts(S, x, S.cand.as<uint64_t>(), S.n_cand, P, st));
   *e = P[3] > 0 ? INFINITY : P[0] + P[1] + P[2];
@@ -1135,6 +1151,10 @@ bal_status bal_adjoint_step(bal_scene* sc, const double* x_t, const double* v_t,
     return BAL_ERR_ARG;
   }
   Scene& S = sc->S;
+  if (S.prm.friction > 0.0) {
+    set_error("bal_adjoint_step: friction > 0 is not differentiated");
+    return BAL_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   BAL_TRY(launch_make_y(S, x_t, v_t, S.d.y, st));
   BAL_TRY(bal_set_al_state(sc, al));

@@ -1,8 +1,10 @@
 // Contact stencils on the GPU, FP64: unsigned point-triangle / edge-edge
 // distances with region classification, the IPC clamped log barrier and the
 // augmented-Lagrangian terms of Eq. (aug-lag), PSD projection of the 12x12
-// stencil Hessian (Sec. 4.2.2), energies for the line search, the conservative
-// step bound and the dual update of Algorithm 1.
+// stencil Hessian (Sec. 4.2.2), the fully-implicit friction of Sec. 4.1 on the
+// same stencils (normal force, normal and closest-point weights lagged at the
+// evaluation point), energies for the line search, the conservative step bound
+// and the dual update of Algorithm 1.
 //
 // Region decisions (which closest-feature formula applies) and the distances
 // used for set membership are computed with explicitly rounded operations
@@ -364,6 +366,72 @@ __device__ void jacobi12(double* A, double* Q) {
   }
 }
 
+// ---- friction (Sec. 4.1) ------------------------------------------------------------
+// Signed weights of the two closest points of a stencil in region R, so that
+// sum_k beta_k X_k runs from the closest point of the second primitive to that
+// of the first (first primitive's weights >= 0).
+__device__ void closest_weights(const d3 X[4], const Region& R, double beta[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) beta[k] = 0.0;
+  if (R.kind == R_PP) {
+    beta[R.n[0]] = 1.0;
+    beta[R.n[1]] = -1.0;
+  } else if (R.kind == R_PE) {
+    const d3 e = X[R.n[2]] - X[R.n[1]];
+    const double t = dot(X[R.n[0]] - X[R.n[1]], e) / dot(e, e);
+    beta[R.n[0]] = 1.0;
+    beta[R.n[1]] = -(1.0 - t);
+    beta[R.n[2]] = -t;
+  } else if (R.kind == R_PT) {
+    // projection of X0 on the triangle's plane: 2x2 normal equations
+    const d3 e1 = X[2] - X[1], e2 = X[3] - X[1], r = X[0] - X[1];
+    const double a11 = dot(e1, e1), a12 = dot(e1, e2), a22 = dot(e2, e2);
+    const double r1 = dot(e1, r), r2 = dot(e2, r);
+    const double det = a11 * a22 - a12 * a12;
+    const double b1 = (a22 * r1 - a12 * r2) / det, b2 = (a11 * r2 - a12 * r1) / det;
+    beta[0] = 1.0;
+    beta[1] = -(1.0 - b1 - b2);
+    beta[2] = -b1;
+    beta[3] = -b2;
+  } else {
+    // line-line closest parameters s (edge a), t (edge b)
+    const d3 u = X[1] - X[0], v = X[3] - X[2], w = X[0] - X[2];
+    const double A = dot(u, u), B = dot(u, v), C = dot(v, v), D = dot(u, w), E = dot(v, w);
+    const double den = A * C - B * B;
+    const double s = (B * E - C * D) / den, t = (A * E - B * D) / den;
+    beta[0] = 1.0 - s;
+    beta[1] = s;
+    beta[2] = -(1.0 - t);
+    beta[3] = -t;
+  }
+  if (beta[0] + beta[1] < 0.0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) beta[k] = -beta[k];
+  }
+}
+
+// Tangent slip w = P sum_k beta_k (X_k - X^t_k) with P = I - nh nh^T.
+__device__ inline d3 tangent_slip(const double beta[4], const d3 X[4], const d3 Xt[4], d3 nh) {
+  d3 u = d3{0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u = u + beta[k] * (X[k] - Xt[k]);
+  return u - dot(u, nh) * nh;
+}
+
+// Mollified slip magnitude f(y) (Sec. 4.1): the printed cubic below eps h,
+// continued linearly (C^2) beyond.
+__device__ inline double fric_f(double y, double eh) {
+  return y < eh ? y * y / eh - y * y * y / (3.0 * eh * eh) : y - eh / 3.0;
+}
+
+// lagged friction set read by the line-search energy
+struct FricLag {
+  const uint64_t* keys;
+  const double *beta, *nrm, *lam, *xt;
+  int64_t n;
+  double chi, eps_h;
+};
+
 struct ContactArgs {
   const uint64_t* keys;
   const uint8_t* flags;
@@ -376,6 +444,13 @@ struct ContactArgs {
   uint64_t* emit_keys;   // [n][6]
   double* emit_vals;     // [n][6][9]
   int project;           // 0: emit the unprojected stencil Hessian (adjoint)
+  // friction (Sec. 4.1), lagged at x: off when fric == 0
+  int fric;
+  double chi, eps_h;     // friction coefficient, eps_v h
+  const double* xt;      // start of the time step
+  double* fr_beta;       // [n][4] lagged weights (written)
+  double* fr_n;          // [n][3] lagged unit normals (written)
+  double* fr_lam;        // [n] lagged normal forces (written)
 };
 
 __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __restrict__ x,
@@ -406,12 +481,49 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
       g2[3 * nd] = acc.x; g2[3 * nd + 1] = acc.y; g2[3 * nd + 2] = acc.z;
     }
     const double cg = p1 / (2.0 * d);
+    // friction: normal force lambda = -phi'(d), normal and weights at x; the
+    // slip w against x^t; D = chi lambda f(|w|), grad = chi lambda a beta_k w,
+    // Hess block (k, l) = chi lambda beta_k beta_l (a P + c w w^T)
+    double beta[4] = {0, 0, 0, 0}, fk = 0.0, fa = 0.0, fcy = 0.0;
+    d3 nh = d3{0, 0, 0}, w = d3{0, 0, 0};
+    if (A.fric) {
+      closest_weights(X, R, beta);
+      d3 nv = d3{0, 0, 0}, Xt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        nv = nv + beta[k] * X[k];
+        Xt[k] = ld3(A.xt, v[k]);
+      }
+      nh = (1.0 / sqrt(dot(nv, nv))) * nv;
+      w = tangent_slip(beta, X, Xt, nh);
+      const double lam = -p1;
+      fk = A.chi * lam;
+      const double y = sqrt(dot(w, w)), eh = A.eps_h;
+      if (y < eh) {
+        fa = 2.0 / eh - y / (eh * eh);
+        fcy = y > 0.0 ? -1.0 / (eh * eh * y) : 0.0;
+      } else {
+        fa = 1.0 / y;
+        fcy = -1.0 / (y * y * y);
+      }
+      if (A.fr_lam) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) A.fr_beta[4 * i + k] = beta[k];
+        A.fr_n[3 * i] = nh.x;
+        A.fr_n[3 * i + 1] = nh.y;
+        A.fr_n[3 * i + 2] = nh.z;
+        A.fr_lam[i] = lam;
+      }
+    }
     bool pin[4];
 #pragma unroll
     for (int nd = 0; nd < 4; ++nd) {
       pin[nd] = S.pinned[v[nd]] != 0;
-      if (!pin[nd] && A.grad)
-        atomic_add3(A.grad, v[nd], d3{cg * g2[3 * nd], cg * g2[3 * nd + 1], cg * g2[3 * nd + 2]});
+      if (!pin[nd] && A.grad) {
+        const double cf = fk * fa * beta[nd];
+        atomic_add3(A.grad, v[nd], d3{cg * g2[3 * nd] + cf * w.x, cg * g2[3 * nd + 1] + cf * w.y,
+                                      cg * g2[3 * nd + 2] + cf * w.z});
+      }
     }
     if (!A.hess) continue;
     // H = c1 g2 g2^T + c2 Hess(d^2)
@@ -454,6 +566,25 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
         }
     } else {
       for (int k = 0; k < 12; ++k) tr += H[13 * k];
+    }
+    if (A.fric && fk > 0.0) {   // friction stencil: PSD by construction, added after the projection
+      const double wv[3] = {w.x, w.y, w.z}, nvv[3] = {nh.x, nh.y, nh.z};
+      double M[3][3];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj)
+          M[ii][jj] = fa * ((ii == jj ? 1.0 : 0.0) - nvv[ii] * nvv[jj]) + fcy * wv[ii] * wv[jj];
+      double b2 = 0.0;
+      for (int nd = 0; nd < 4; ++nd) {
+        b2 += beta[nd] * beta[nd];
+        for (int md = 0; md < 4; ++md) {
+          const double s = fk * beta[nd] * beta[md];
+          for (int ii = 0; ii < 3; ++ii)
+            for (int jj = 0; jj < 3; ++jj) H[12 * (3 * nd + ii) + 3 * md + jj] += s * M[ii][jj];
+        }
+      }
+      tr += fk * b2 * (M[0][0] + M[1][1] + M[2][2]);
     }
     tr *= (1.0 / 12.0);
 #pragma unroll
@@ -504,7 +635,7 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
                                                        const uint64_t* __restrict__ apk,
                                                        const double* __restrict__ apmu,
                                                        const double* __restrict__ aps, int64_t nap,
-                                                       double sigma, double* partials, int nblk) {
+                                                       double sigma, FricLag F, double* partials, int nblk) {
   double e = 0.0, cnt = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < nc; i += (int64_t)gridDim.x * NT) {
     int v[4];
@@ -523,6 +654,21 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
     const double d = pair_distance(S, x, apk[i], v, X, R);
     const double c2 = S.dhat + aps[i];
     e += apmu[i] * (c2 - d) + sigma * bar(d, c2);
+  }
+  // friction with the lagged weights, normals and forces
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < F.n; i += (int64_t)gridDim.x * NT) {
+    int v[4];
+    pair_nodes(S, F.keys[i], v);
+    d3 X[4], Xt[4];
+    double beta[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      X[k] = ld3(x, v[k]);
+      Xt[k] = ld3(F.xt, v[k]);
+      beta[k] = F.beta[4 * i + k];
+    }
+    const d3 w = tangent_slip(beta, X, Xt, ld3(F.nrm, (int)i));
+    e += F.chi * F.lam[i] * fric_f(sqrt(dot(w, w)), F.eps_h);
   }
   e = block_sum<double, NT>(e);
   cnt = block_sum<double, NT>(cnt);
@@ -807,6 +953,10 @@ bal_status launch_pair_distance(Scene& S, const double* x, const uint64_t* keys,
 
 bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool hess,
                                 cudaStream_t st) {
+  // friction lagged at x: on for the projected (time-step) Hessian, off for the
+  // sigma0 evaluation and the adjoint
+  const bool fric = S.prm.friction > 0.0 && S.project && !S.fric_suspend;
+  if (fric) S.n_fr = 0;
   if (S.n_eval <= 0) return BAL_OK;
   ContactArgs A;
   A.keys = S.eval_keys.as<uint64_t>();
@@ -824,6 +974,23 @@ bal_status launch_contact_terms(Scene& S, const double* x, double* grad, bool he
   }
   A.emit_keys = S.emit_keys.as<uint64_t>();
   A.emit_vals = S.emit_vals.as<double>();
+  A.fric = fric ? 1 : 0;
+  A.chi = S.prm.friction;
+  A.eps_h = (S.prm.friction_eps_v > 0.0 ? S.prm.friction_eps_v : S.d.dhat) * S.d.h;
+  A.xt = S.xt;
+  A.fr_beta = A.fr_n = A.fr_lam = nullptr;
+  if (A.fric) {
+    BAL_TRY(buf_reserve(S.fr_keys, sizeof(uint64_t) * (S.n_eval + 1)));
+    BAL_TRY(buf_reserve(S.fr_beta, sizeof(double) * 4 * (S.n_eval + 1)));
+    BAL_TRY(buf_reserve(S.fr_n, sizeof(double) * 3 * (S.n_eval + 1)));
+    BAL_TRY(buf_reserve(S.fr_lam, sizeof(double) * (S.n_eval + 1)));
+    BAL_CUDA(cudaMemcpyAsync(S.fr_keys.p, S.eval_keys.p, sizeof(uint64_t) * S.n_eval,
+                             cudaMemcpyDeviceToDevice, st));
+    A.fr_beta = S.fr_beta.as<double>();
+    A.fr_n = S.fr_n.as<double>();
+    A.fr_lam = S.fr_lam.as<double>();
+    S.n_fr = S.n_eval;
+  }
   k_contact_terms<<<grid_for(S.n_eval, 128, kNumSM * 8), 128, 0, st>>>(S.d, x, A);
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
@@ -835,9 +1002,18 @@ bal_status launch_contact_energy(Scene& S, const double* x, const uint64_t* cand
   constexpr int NT = 256;
   const int nblk = 2 * kNumSM;
   const int64_t nap = (int64_t)S.ap_keys.size();
+  FricLag F;
+  F.keys = S.fr_keys.as<uint64_t>();
+  F.beta = S.fr_beta.as<double>();
+  F.nrm = S.fr_n.as<double>();
+  F.lam = S.fr_lam.as<double>();
+  F.xt = S.xt;
+  F.n = S.prm.friction > 0.0 ? S.n_fr : 0;
+  F.chi = S.prm.friction;
+  F.eps_h = (S.prm.friction_eps_v > 0.0 ? S.prm.friction_eps_v : S.d.dhat) * S.d.h;
   k_contact_energy<NT><<<nblk, NT, 0, st>>>(S.d, x, cand, ncand, S.ap_keys_d.as<uint64_t>(),
                                             S.ap_mu_d.as<double>(), S.ap_s_d.as<double>(), nap,
-                                            S.sigma, S.partials, nblk);
+                                            S.sigma, F, S.partials, nblk);
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   BAL_TRY(finish_reduce_offset(S, 0, nblk, slot, RED_SUM, st));

@@ -124,6 +124,11 @@ struct Scene {
   Buf flags;                     // per-pair selection flags
   Buf eval_keys, eval_flags, eval_mu, eval_s;   // evaluation list A u A'
   int64_t n_eval = 0;
+  // friction (Sec. 4.1) lagged at the last contact-term evaluation: pair keys,
+  // closest-point weights [n][4], unit normals [n][3], normal forces [n]
+  Buf fr_keys, fr_beta, fr_n, fr_lam;
+  int64_t n_fr = 0;
+  bool fric_suspend = false;     // sigma0 evaluation: barrier gradient only
   Buf ls_cand, ls_cand_alt;      // line-search candidates
   int64_t n_ls_cand = 0;
 

@@ -38,6 +38,17 @@ def test_default_params_follow_the_paper(lib):
     assert p.newton_tol == 1e-4 and p.pcg_tol == 1e-4 and p.pcg_stall_window == 100
     assert p.ap_ratio == 1e-2 and p.sigma_growth == 1.2 and p.sigma_cap == 100.0
     assert p.ls_min_alpha == 1e-9 and p.ls_extra_pcg == 100
+    assert p.friction == 0.0 and p.friction_eps_v == 0.0      # frictionless unless asked
+
+
+@pytest.mark.parametrize("field,value", [("friction", -0.1), ("friction_eps_v", -1.0),
+                                         ("step_bound", 1.0), ("al_mode", 7)])
+def test_create_scene_rejects_invalid_params(lib, field, value):
+    """Parameters are validated on the host before any device allocation."""
+    from paper_2407_00046_b300 import scenes
+    with pytest.raises(bal.BalError) as e:
+        bal.Scene(scenes.two_cubes(n=1), bal.default_params(**{field: value}))
+    assert e.value.status == 1
 
 
 def test_last_error_is_a_string(lib):

@@ -1,0 +1,118 @@
+"""GPU parity of the fully-implicit friction of Sec. 4.1 through the C ABI:
+gradient, Hessian, Lambda and energy with friction lagged at x against the
+oracle in the static and sliding zones, time-step trajectories of a sliding
+cube against the oracle, and Coulomb's law on larger cubes (a property that
+holds at any size)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bal as obal  # noqa: E402
+from oracle import system  # noqa: E402
+from paper_2407_00046_b300 import bal, scenes  # noqa: E402
+
+from gpu_common import gpu_hessian, oracle_state  # noqa: E402
+
+DEV = "cuda"
+CHI = 0.3
+TOL = 1e-10
+T_DIR = np.array([1.0, 0.0, 1.0]) / np.sqrt(2.0)
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+@pytest.mark.parametrize("zone,slip", [("static", 2e-6), ("sliding", 1e-2)])
+@pytest.mark.parametrize("with_ap", [False, True])
+def test_friction_assembly_matches_oracle(zone, slip, with_ap):
+    sc = scenes.sliding_cube()
+    rng = np.random.default_rng(21)
+    c = sc.body == 0
+    x = sc.X.copy()
+    x[c] += slip * T_DIR + 2e-8 * rng.normal(size=(int(c.sum()), 3))
+    S = bal.Scene(sc, bal.default_params(friction=CHI))
+    S.step_begin(T(sc.X), T(sc.V0))
+    sigma = 4.0
+    ap = {}
+    if with_ap:
+        m = system.make_model(sc)
+        keys, _ = obal.active_pairs(m, x)
+        ap = {k: 0.3 * (i % 3) for i, k in enumerate(keys[::3])}
+    S.set_al_state(sigma, sigma, [bal.pair_key(*k) for k in sorted(ap)], [ap[k] for k in sorted(ap)])
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    view = S.assemble_hessian(T(x), g)
+    Hg, lam_g, _ = gpu_hessian(S, view)
+    m, y, ps = oracle_state(sc, x, sigma, ap)
+    fs = obal.friction_set(m, x, sc.X, ps, sigma, obal.Params(friction=CHI))
+    w = np.einsum("nk,nkc->nc", fs.beta, x[fs.nodes] - sc.X[fs.nodes])
+    ymax = np.linalg.norm(w, axis=1).max()
+    assert (ymax < fs.eps_h) if zone == "static" else (ymax > fs.eps_h)
+    g_or = system.gradient(m, x, y, ps, sigma, fric=fs).ravel()
+    H_or, lam_or = system.hessian(m, x, y, ps, sigma, with_lambda=True, fric=fs)
+    g_nf = system.gradient(m, x, y, ps, sigma).ravel()
+    assert np.abs(g_or - g_nf).max() > 1e-3 * np.abs(g_or).max()   # friction is visible
+    gerr = np.abs(g.cpu().numpy() - g_or).max() / np.abs(g_or).max()
+    herr = np.abs((Hg - H_or).toarray()).max() / np.abs(H_or.toarray()).max()
+    lerr = np.abs(lam_g - lam_or).max() / np.abs(lam_or).max()
+    assert gerr < TOL, gerr
+    assert herr < TOL, herr
+    assert lerr < TOL, lerr
+    e_or = system.energy(m, x, y, ps, sigma, fs)
+    assert S.energy(T(x)) == pytest.approx(e_or, rel=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["ca-grid", "ccd-lbvh"])
+def test_sliding_cube_trajectory_matches_oracle(mode):
+    sc = scenes.sliding_cube()
+    step_mode, broad = mode.split("-")
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-9, pcg_tol=1e-12, pcg_max_iter=20000,
+                                         newton_max_iter=300, friction=CHI,
+                                         step_mode=bal.STEP_CCD if step_mode == "ccd" else bal.STEP_CA,
+                                         broad_phase=bal.BROAD_LBVH if broad == "lbvh" else bal.BROAD_GRID))
+    m = system.make_model(sc)
+    x, v = T(sc.X), T(sc.V0)
+    xo, vo = sc.X.copy(), sc.V0.copy()
+    for _ in range(2):
+        info = S.time_step(x, v)
+        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-9, newton_max=300, friction=CHI,
+                                                           step_mode=step_mode, broad_phase=broad))
+        assert info["converged"] == 1 and io["converged"]
+        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+        assert np.abs(v.cpu().numpy() - vo).max() < 1e-8 / sc.h
+
+
+@pytest.mark.parametrize("n_cube", [3, 12])
+def test_coulomb_law_on_gpu(n_cube):
+    """The converged step's tangential impulse on the sliding cube is chi times
+    its normal impulse, at any resolution of the cube."""
+    sc = scenes.sliding_cube(n_cube=n_cube)
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-9, pcg_tol=1e-12, pcg_max_iter=50000,
+                                         newton_max_iter=300, friction=CHI,
+                                         step_mode=bal.STEP_CCD, broad_phase=bal.BROAD_LBVH))
+    m = system.make_model(sc)
+    c = sc.body == 0
+    M = m.mass[c].sum()
+    x, v = T(sc.X), T(sc.V0)
+    for _ in range(3):
+        vb = (m.mass[c, None] * v.cpu().numpy()[c]).sum(axis=0) / M
+        info = S.time_step(x, v)
+        assert info["converged"] == 1
+        va = (m.mass[c, None] * v.cpu().numpy()[c]).sum(axis=0) / M
+        dv = va - vb
+        ratio = -(dv @ T_DIR) / (dv[1] - sc.gravity[1] * sc.h)
+        assert abs(ratio - CHI) < 1e-5, ratio
+        assert va @ T_DIR > 0.3
+
+
+def test_adjoint_refuses_friction():
+    sc = scenes.sliding_cube()
+    S = bal.Scene(sc, bal.default_params(friction=CHI))
+    z = torch.zeros(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    dE = torch.zeros(sc.n_tets, dtype=torch.float64, device=DEV)
+    al = dict(sigma=1.0, sigma0=1.0, dmin_prev=float("inf"), ap_keys=[], ap_mu=[])
+    with pytest.raises(bal.BalError) as e:
+        S.adjoint_step(T(sc.X), T(sc.V0), T(sc.X), al, z, z, dE)
+    assert e.value.status == 1   # BAL_ERR_ARG
