@@ -106,7 +106,7 @@ PRECONDS = {"block-jacobi": 0, "warm-start": 1, "additive": 2}   # bal_precond v
 STEP_MODES = {"ca": 0, "ccd": 1}                     # bal_step_mode values
 BROAD_PHASES = {"grid": 0, "lbvh": 1}                # bal_broad_phase values
 AL_MODES = {"algorithm1": 0, "plain": 1}             # bal_al_mode values
-PCG_TOL_MODES = {"fixed": 0, "truncated-newton": 1}  # bal_pcg_tol_mode values
+PCG_TOL_MODES = {"fixed": 0, "truncated-newton": 1, "cond-x": 2, "cond-b": 3}  # bal_pcg_tol_mode values
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
 
 

@@ -101,8 +101,18 @@ typedef struct {
  * held at sigma0, A' empty, no dual update. */
 typedef enum { BAL_AL_ALGORITHM1 = 0, BAL_AL_PLAIN = 1 } bal_al_mode;
 /* FIXED: ||r|| <= pcg_tol ||r_0|| on every solve. TRUNCATED_NEWTON: App. B
- * criterion (i), ||r|| <= min(0.5, sqrt(||e||)) ||e|| with e the gradient. */
-typedef enum { BAL_PCG_TOL_FIXED = 0, BAL_PCG_TOL_TRUNCATED_NEWTON = 1 } bal_pcg_tol_mode;
+ * criterion (i), ||r|| <= min(0.5, sqrt(||e||)) ||e|| with e the gradient.
+ * COND_X / COND_B: App. B criteria (ii) ||r|| <= u kappa ||x_k|| and (iii)
+ * ||r|| <= u kappa ||b|| with u = DBL_EPSILON, x_k the Newton iterate, b = -e
+ * and kappa = max / min of the assembled eigenvalue stiffness Lambda over free
+ * DOFs (elastic, contact and friction stencils plus the lumped mass); the
+ * relative tolerance these give is capped at 0.5. */
+typedef enum {
+  BAL_PCG_TOL_FIXED = 0,
+  BAL_PCG_TOL_TRUNCATED_NEWTON = 1,
+  BAL_PCG_TOL_COND_X = 2,
+  BAL_PCG_TOL_COND_B = 3
+} bal_pcg_tol_mode;
 
 /* Step bound of the line search. CA: conservative advancement on the distance
  * (every pair keeps (1 - step_bound) of its gap). CCD: the cubic CCD of
@@ -199,6 +209,8 @@ typedef struct {
   double ms_assemble, ms_solve, ms_line_search, ms_contact;
   double ms_ls_broad, ms_ls_bound, ms_ls_energy;   /* line-search breakdown */
   int64_t n_raw_candidates;   /* line-search pairs from the broad phase, before filtering */
+  double pcg_tol;             /* relative PCG tolerance the solve used */
+  double kappa;               /* Lambda max / min over free DOFs (COND_X / COND_B; else 0) */
 } bal_newton_info;
 
 typedef struct {

@@ -23,7 +23,7 @@ PRECOND_BJ, PRECOND_BJ_WARMSTART, PRECOND_ADDITIVE = 0, 1, 2
 STEP_CA, STEP_CCD = 0, 1
 BROAD_GRID, BROAD_LBVH = 0, 1
 AL_ALGORITHM1, AL_PLAIN = 0, 1
-PCG_TOL_FIXED, PCG_TOL_TRUNCATED_NEWTON = 0, 1
+PCG_TOL_FIXED, PCG_TOL_TRUNCATED_NEWTON, PCG_TOL_COND_X, PCG_TOL_COND_B = 0, 1, 2, 3
 
 
 class BalError(RuntimeError):
@@ -88,7 +88,8 @@ class NewtonInfo(C.Structure):
                 ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
                 ("ms_line_search", C.c_double), ("ms_contact", C.c_double),
                 ("ms_ls_broad", C.c_double), ("ms_ls_bound", C.c_double),
-                ("ms_ls_energy", C.c_double), ("n_raw_candidates", C.c_int64)]
+                ("ms_ls_energy", C.c_double), ("n_raw_candidates", C.c_int64),
+                ("pcg_tol", C.c_double), ("kappa", C.c_double)]
 
 
 class StepInfo(C.Structure):

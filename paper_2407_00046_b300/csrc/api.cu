@@ -6,6 +6,7 @@
 // operation runs in the CUDA kernels of this library.
 #include <atomic>
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -391,9 +392,28 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
   BAL_TRY(launch_axpy(S, n3, -1.0, S.grad, S.gtmp, S.gtmp, st));   // gtmp = -grad
   BAL_CUDA(cudaMemsetAsync(S.dir, 0, sizeof(double) * n3, st));
   bal_solve_info si;
-  // per-solve tolerance: fixed, or App. B criterion (i) min(0.5, sqrt(||e||)) (x0 = 0, so r0 = -e)
-  const double tol = S.prm.pcg_tol_mode == BAL_PCG_TOL_TRUNCATED_NEWTON ? std::min(0.5, std::sqrt(en))
-                                                                        : S.prm.pcg_tol;
+  // per-solve tolerance relative to ||r0|| = ||e|| (x0 = 0): fixed, or App. B
+  // criteria (i) min(0.5, sqrt(||e||)), (ii) u kappa ||x_k|| / ||e||, (iii) u kappa
+  double tol = S.prm.pcg_tol;
+  if (S.prm.pcg_tol_mode == BAL_PCG_TOL_TRUNCATED_NEWTON) {
+    tol = std::min(0.5, std::sqrt(en));
+  } else if (S.prm.pcg_tol_mode == BAL_PCG_TOL_COND_X || S.prm.pcg_tol_mode == BAL_PCG_TOL_COND_B) {
+    BAL_TRY(launch_lambda_range(S, 20, st));
+    double lr[2];
+    BAL_TRY(read_scalars(S, lr, 20, 2, st));
+    I.kappa = lr[1] > 0.0 ? lr[0] / lr[1] : INFINITY;
+    const double u = DBL_EPSILON;
+    if (S.prm.pcg_tol_mode == BAL_PCG_TOL_COND_B) {
+      tol = u * I.kappa;
+    } else {
+      BAL_TRY(launch_dot(S, n3, x, x, 22, st));
+      double xx;
+      BAL_TRY(read_scalars(S, &xx, 22, 1, st));
+      tol = u * I.kappa * std::sqrt(xx) / en;
+    }
+    tol = std::min(tol, 0.5);
+  }
+  I.pcg_tol = tol;
   BAL_TRY(pcg_solve(S, S.gtmp, S.dir, tol, S.prm.pcg_max_iter, &si, st));
   I.pcg_iters = si.iters;
   I.pcg_rel_residual = si.rel_residual;
@@ -531,7 +551,7 @@ static bool params_ok(const bal_params* p) {
       p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
       p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||
       p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||
-      p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_TRUNCATED_NEWTON ||
+      p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_COND_B ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
       !(p->friction >= 0) || !(p->friction_eps_v >= 0));
 }

@@ -265,6 +265,8 @@ bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y
 bal_status launch_axpy(Scene& S, int64_t n, double a, const double* x, const double* y, double* out,
                        cudaStream_t st);
 bal_status launch_dot(Scene& S, int64_t n, const double* a, const double* b, int slot, cudaStream_t st);
+// S.scal[slot] = max, S.scal[slot + 1] = min of Lambda over free DOFs
+bal_status launch_lambda_range(Scene& S, int slot, cudaStream_t st);
 // S.scal[slot] = max over surface vertices of |d_v|
 bal_status launch_surf_max_norm(Scene& S, const double* d, int slot, cudaStream_t st);
 

@@ -47,7 +47,34 @@ __global__ void __launch_bounds__(NT) k_surf_max_norm(Dev S, const double* __res
   if (threadIdx.x == 0) partials[blockIdx.x] = m;
 }
 
+// max and min of the assembled eigenvalue stiffness Lambda over free DOFs
+// (App. B condition-number estimate): partials [0, nb) max, [nb, 2 nb) min
+template <int NT>
+__global__ void __launch_bounds__(NT) k_lambda_range(Dev S, double* partials, int nb) {
+  double hi = 0.0, lo = INFINITY;
+  for (int v = blockIdx.x * NT + threadIdx.x; v < S.nv; v += gridDim.x * NT) {
+    if (S.pinned[v]) continue;
+    const d3 l = ld3(S.Lambda, v);
+    hi = fmax(hi, fmax(l.x, fmax(l.y, l.z)));
+    lo = fmin(lo, fmin(l.x, fmin(l.y, l.z)));
+  }
+  hi = block_max<double, NT>(hi, 0.0);
+  lo = block_min<double, NT>(lo, INFINITY);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = hi;
+    partials[nb + blockIdx.x] = lo;
+  }
+}
+
 }  // namespace
+
+bal_status launch_lambda_range(Scene& S, int slot, cudaStream_t st) {
+  k_lambda_range<256><<<kRB, 256, 0, st>>>(S.d, S.partials, kRB);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(finish_reduce_offset(S, 0, kRB, slot, RED_MAX, st));
+  return finish_reduce_offset(S, kRB, kRB, slot + 1, RED_MIN, st);
+}
 
 bal_status launch_make_y(Scene& S, const double* xt, const double* vt, double* y, cudaStream_t st) {
   k_make_y<<<grid_for(S.d.nv), kThreads, 0, st>>>(S.d, xt, vt, S.grav[0], S.grav[1], S.grav[2], y);

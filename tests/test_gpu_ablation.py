@@ -1,5 +1,6 @@
 """GPU parity of the ablation modes (the plain inexact Newton method; the
-truncated-Newton PCG tolerance of App. B) against the oracle."""
+truncated-Newton and condition-number PCG tolerances of App. B) against the
+oracle."""
 import numpy as np
 import pytest
 
@@ -67,3 +68,40 @@ def test_truncated_newton_tolerance_rule_and_stationary_end_state():
     g = system.gradient(m, xe, y, obal.make_pairset(m, xe, keys, Ap, sigma), sigma)
     g0 = system.gradient(m, x0, y, obal.make_pairset(m, x0, [], {}, sigma), sigma)
     assert np.linalg.norm(g) <= 1e-10 * np.linalg.norm(g0)
+
+
+@pytest.mark.parametrize("mode", ["cond-x", "cond-b"])
+def test_condition_number_tolerance_rules(mode):
+    """Criteria (ii) and (iii) of App. B: kappa = max / min of the assembled
+    eigenvalue stiffness over free DOFs equals the oracle's, each solve's
+    relative tolerance is u kappa ||x_k|| / ||e|| (ii) or u kappa (iii), capped
+    at 0.5, and the step ends at the oracle's minimiser."""
+    sc = close_cubes(n=2, gap=5e-4)
+    pm = bal.PCG_TOL_COND_X if mode == "cond-x" else bal.PCG_TOL_COND_B
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_max_iter=20000, pcg_tol_mode=pm))
+    m = system.make_model(sc)
+    y = system.inertia_target(m, sc.X, sc.V0)
+    x, v = T(sc.X), T(sc.V0)
+    S.step_begin(x, v)
+    u = np.finfo(np.float64).eps
+    for k in range(200):
+        xb = x.cpu().numpy().reshape(-1, 3).copy()
+        info = S.newton_step(x)
+        if info["converged"]:
+            break
+        if k < 4:
+            al = S.get_al_state()
+            Ap = {bal.unpack_key(kk): mu for kk, mu in zip(al["ap_keys"], al["ap_mu"])}
+            keys, _ = obal.active_pairs(m, xb)
+            ps = obal.make_pairset(m, xb, keys, Ap, al["sigma"])
+            _, lam = system.hessian(m, xb, y, ps, al["sigma"], with_lambda=True)
+            lf = lam.reshape(-1, 3)[m.free]
+            kappa = lf.max() / lf.min()
+            assert info["kappa"] == pytest.approx(kappa, rel=1e-10)
+            tol = u * kappa * (np.linalg.norm(xb) / info["grad_norm"] if mode == "cond-x" else 1.0)
+            assert info["pcg_tol"] == pytest.approx(min(tol, 0.5), rel=1e-10)
+        assert info["pcg_rel_residual"] <= max(info["pcg_tol"], 1e-10) * (1 + 1e-9), (k, info)
+    assert info["converged"] == 1
+    xo, _, io = obal.time_step(m, sc.X, sc.V0, obal.Params(newton_tol=1e-8))
+    assert io["converged"]
+    assert np.abs(x.cpu().numpy().reshape(-1, 3) - xo).max() < 1e-8
