@@ -101,13 +101,13 @@ class Clocks:
 FP64_PEAK_TFLOPS = 1.128
 
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}     # bal_precision values
+PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2, "fp32": 3}     # bal_precision values
 PRECONDS = {"block-jacobi": 0, "warm-start": 1, "additive": 2}   # bal_precond values
 STEP_MODES = {"ca": 0, "ccd": 1}                     # bal_step_mode values
 BROAD_PHASES = {"grid": 0, "lbvh": 1}                # bal_broad_phase values
 AL_MODES = {"algorithm1": 0, "plain": 1}             # bal_al_mode values
 PCG_TOL_MODES = {"fixed": 0, "truncated-newton": 1, "cond-x": 2, "cond-b": 3}  # bal_pcg_tol_mode values
-DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64"}
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "df64": "df64+f64", "fp32": "f32+f64"}
 
 
 def spmv_kernel_bytes(precision, nv, nnzL, nnzC):
@@ -118,13 +118,13 @@ def spmv_kernel_bytes(precision, nv, nnzL, nnzC):
     per block, the row pointer -- plus one read of p and one write of q. The
     column-side index lists and the second (L2) read of each block for its
     transpose are this kernel's overhead, not algorithmic.
-    fp64 / mixed (k_pcg_offdiag): lower blocks with their row and column index,
+    fp64 / mixed / fp32 (k_pcg_offdiag): lower blocks with their row and column index,
     one read of p, q read and written once."""
     nb = nnzL + nnzC
     if precision == "df64":
         return ("k_dd_spmv (symmetric H p, double-float gather)",
                 (nv + nb) * 72 + nb * 4 + (nv + 1) * 4 + 2 * 24 * nv)
-    p = 4 if precision == "mixed" else 8
+    p = 4 if precision in ("mixed", "fp32") else 8
     return "k_pcg_offdiag (symmetric off-diagonal blocks, atomics)", nb * (9 * p + 8) + 3 * 3 * nv * p
 
 

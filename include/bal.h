@@ -47,7 +47,12 @@ typedef enum {
  * refinement. DF64: PCG recurrences in double-float arithmetic (pairs of FP32,
  * ~47-bit significand) with FP64 residuals deciding convergence; falls back to
  * FP64 for a matrix with an entry beyond 1e36. */
-typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2 } bal_precision;
+/* FP32: the single-precision path (the paper's single-precision version,
+ * Sec. 6): element stencil eigensystems evaluated in FP32 arithmetic, plus the
+ * MIXED solver (FP32 matrix copy, SpMV, preconditioner and PCG vectors, FP64
+ * refinement). Contact distances, barrier derivatives, the gradient, the
+ * residual norms and the line-search energies stay FP64. */
+typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2, BAL_PREC_FP32 = 3 } bal_precision;
 /* BJ: block-Jacobi. BJ_WARMSTART: block-Jacobi after the stiffness-grouped
  * warm start (Sec. 4.2.2). ADDITIVE: the two-level additive preconditioner the
  * paper compares against (App. A): 3x3 diagonal-block inverses plus exact

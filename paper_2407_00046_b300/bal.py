@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libbal.so")
 OK = 0
 STATUS = {0: "OK", 1: "ARG", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
           6: "CUDA", 7: "LINE_SEARCH", 8: "STATE"}
-PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
+PREC_FP64, PREC_MIXED, PREC_DF64, PREC_FP32 = 0, 1, 2, 3
 PRECOND_BJ, PRECOND_BJ_WARMSTART, PRECOND_ADDITIVE = 0, 1, 2
 STEP_CA, STEP_CCD = 0, 1
 BROAD_GRID, BROAD_LBVH = 0, 1

@@ -546,7 +546,7 @@ uint64_t bal_launch_count(void) { return g_launches.load(std::memory_order_relax
 
 static bool params_ok(const bal_params* p) {
   return p && !(!(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
-      p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_DF64 ||
+      p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_FP32 ||
       p->precond < BAL_PRECOND_BJ || p->precond > BAL_PRECOND_ADDITIVE ||
       p->step_mode < BAL_STEP_CA || p->step_mode > BAL_STEP_CCD ||
       p->broad_phase < BAL_BROAD_GRID || p->broad_phase > BAL_BROAD_LBVH ||

@@ -1,4 +1,5 @@
-// Neo-Hookean tetrahedral elasticity and inertia (Sec. 3.1) on the GPU, FP64.
+// Neo-Hookean tetrahedral elasticity and inertia (Sec. 3.1) on the GPU: FP64,
+// with the element stencil Hessians optionally in FP32 (single-precision path).
 //
 // Psi(F) = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2 (the NH of IPC; the
 // paper names the model only). The element stencil Hessian is projected to PSD
@@ -50,36 +51,60 @@ __device__ inline double det3(const double F[3][3]) {
          F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
 }
 
+// F = Ds Dm^{-1} in arithmetic T: the edge vectors x_{a+1} - x_0 are formed in
+// FP64 (absolute coordinates would cancel in FP32), then rounded to T.
+template <typename T>
+__device__ inline void def_grad_t(const d3 X[4], const double* __restrict__ Mi, T F[3][3]) {
+  const d3 e[3] = {X[1] - X[0], X[2] - X[0], X[3] - X[0]};
+  T m[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = (T)Mi[k];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T ei[3] = {(T)(i == 0 ? e[0].x : (i == 1 ? e[0].y : e[0].z)),
+                     (T)(i == 0 ? e[1].x : (i == 1 ? e[1].y : e[1].z)),
+                     (T)(i == 0 ? e[2].x : (i == 1 ? e[2].y : e[2].z))};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[i][j] = ei[0] * m[j] + ei[1] * m[3 + j] + ei[2] * m[6 + j];
+  }
+}
+
+// squared relative off-diagonal size at which the 3x3 Jacobi iteration stops
+template <typename T> struct JacobiTol;
+template <> struct JacobiTol<double> { static constexpr double v = 1e-34; };
+template <> struct JacobiTol<float> { static constexpr float v = 1e-14f; };
+
 // Cyclic Jacobi for a symmetric 3x3 (in place). A ends (nearly) diagonal; V
 // holds the eigenvectors in its columns.
-__device__ inline void jacobi3(double A[3][3], double V[3][3]) {
+template <typename T>
+__device__ inline void jacobi3(T A[3][3], T V[3][3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? T(1) : T(0);
   for (int sweep = 0; sweep < 12; ++sweep) {
-    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-    const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
-    if (off <= 1e-34 * dia || off == 0.0) break;
+    const T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const T dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= JacobiTol<T>::v * dia || off == T(0)) break;
 #pragma unroll
     for (int pq = 0; pq < 3; ++pq) {
       const int p = pq == 2 ? 1 : 0;
       const int q = pq == 0 ? 1 : 2;
-      const double apq = A[p][q];
-      if (apq == 0.0) continue;
-      const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-      const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-      const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+      const T apq = A[p][q];
+      if (apq == T(0)) continue;
+      const T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
+      const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+      const T c = T(1) / sqrt(t * t + T(1)), s = t * c;
       const int r = 3 - p - q;
-      const double arp = A[r][p], arq = A[r][q];
+      const T arp = A[r][p], arq = A[r][q];
       A[p][p] -= t * apq;
       A[q][q] += t * apq;
-      A[p][q] = A[q][p] = 0.0;
+      A[p][q] = A[q][p] = T(0);
       A[r][p] = A[p][r] = c * arp - s * arq;
       A[r][q] = A[q][r] = s * arp + c * arq;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const double vkp = V[k][p], vkq = V[k][q];
+        const T vkp = V[k][p], vkq = V[k][q];
         V[k][p] = c * vkp - s * vkq;
         V[k][q] = s * vkp + c * vkq;
       }
@@ -89,64 +114,79 @@ __device__ inline void jacobi3(double A[3][3], double V[3][3]) {
 
 // Signed SVD F = U diag(s) V^T with det U = det V = +1, s descending in
 // magnitude; s[2] carries the sign of det F.
-__device__ inline void svd3(const double F[3][3], double U[3][3], double s[3], double V[3][3]) {
-  double C[3][3];
+template <typename T>
+__device__ inline void svd3(const T F[3][3], T U[3][3], T s[3], T V[3][3]) {
+  T C[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) C[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
-  jacobi3(C, V);
-  double w[3] = {C[0][0], C[1][1], C[2][2]};
+  jacobi3<T>(C, V);
+  T w[3] = {C[0][0], C[1][1], C[2][2]};
   // sort descending (swap columns of V)
 #pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       if (w[i] < w[i + 1]) {
-        const double tw = w[i]; w[i] = w[i + 1]; w[i + 1] = tw;
+        const T tw = w[i]; w[i] = w[i + 1]; w[i + 1] = tw;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const double tv = V[k][i]; V[k][i] = V[k][i + 1]; V[k][i + 1] = tv;
+          const T tv = V[k][i]; V[k][i] = V[k][i + 1]; V[k][i + 1] = tv;
         }
       }
     }
   }
-  const double dV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
-                    V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
-                    V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
-  if (dV < 0) {
+  const T dV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
+               V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+               V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+  if (dV < T(0)) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) V[k][2] = -V[k][2];
   }
-  d3 Fv[3];
+  // columns of F V; U by Gram-Schmidt on the first two, the third by a cross product
+  T Fv[3][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
-    Fv[c] = d3{F[0][0] * V[0][c] + F[0][1] * V[1][c] + F[0][2] * V[2][c],
-               F[1][0] * V[0][c] + F[1][1] * V[1][c] + F[1][2] * V[2][c],
-               F[2][0] * V[0][c] + F[2][1] * V[1][c] + F[2][2] * V[2][c]};
-  d3 u0 = (1.0 / sqrt(dot(Fv[0], Fv[0]))) * Fv[0];
-  d3 t1 = Fv[1] - dot(u0, Fv[1]) * u0;
-  d3 u1 = (1.0 / sqrt(dot(t1, t1))) * t1;
-  d3 u2 = cross(u0, u1);
-  s[0] = dot(u0, Fv[0]);
-  s[1] = dot(u1, Fv[1]);
-  s[2] = dot(u2, Fv[2]);
-  U[0][0] = u0.x; U[1][0] = u0.y; U[2][0] = u0.z;
-  U[0][1] = u1.x; U[1][1] = u1.y; U[2][1] = u1.z;
-  U[0][2] = u2.x; U[1][2] = u2.y; U[2][2] = u2.z;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Fv[c][i] = F[i][0] * V[0][c] + F[i][1] * V[1][c] + F[i][2] * V[2][c];
+  const T n0 = T(1) / sqrt(Fv[0][0] * Fv[0][0] + Fv[0][1] * Fv[0][1] + Fv[0][2] * Fv[0][2]);
+  T u0[3], t1[3], u1[3], u2[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u0[i] = n0 * Fv[0][i];
+  const T p01 = u0[0] * Fv[1][0] + u0[1] * Fv[1][1] + u0[2] * Fv[1][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t1[i] = Fv[1][i] - p01 * u0[i];
+  const T n1 = T(1) / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u1[i] = n1 * t1[i];
+  u2[0] = u0[1] * u1[2] - u0[2] * u1[1];
+  u2[1] = u0[2] * u1[0] - u0[0] * u1[2];
+  u2[2] = u0[0] * u1[1] - u0[1] * u1[0];
+  s[0] = u0[0] * Fv[0][0] + u0[1] * Fv[0][1] + u0[2] * Fv[0][2];
+  s[1] = u1[0] * Fv[1][0] + u1[1] * Fv[1][1] + u1[2] * Fv[1][2];
+  s[2] = u2[0] * Fv[2][0] + u2[1] * Fv[2][1] + u2[2] * Fv[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    U[i][0] = u0[i];
+    U[i][1] = u1[i];
+    U[i][2] = u2[i];
+  }
 }
 
 // H (upper triangle of a symmetric 9x9, row-major packed 45) += lam w w^T
-__device__ inline void rank1_45(double H[45], const double w[9], double lam) {
+template <typename T>
+__device__ inline void rank1_45(T H[45], const T w[9], T lam) {
   int k = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const double li = lam * w[i];
+    const T li = lam * w[i];
 #pragma unroll
     for (int j = i; j < 9; ++j) H[k++] += li * w[j];
   }
 }
-__device__ inline double h45(const double H[45], int i, int j) {
+template <typename T>
+__device__ inline T h45(const T H[45], int i, int j) {
   if (i > j) { const int t = i; i = j; j = t; }
   return H[i * 9 - (i * (i - 1)) / 2 + (j - i)];
 }
@@ -224,74 +264,79 @@ __device__ inline void add_block(double* dst, const double blk[3][3], bool trans
     for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, transpose ? blk[k][i] : blk[i][k]);
 }
 
+// Element stencil Hessians in arithmetic T (double: the FP64 path; float: the
+// single-precision path), accumulated into the FP64 block storage.
+template <typename T>
 __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __restrict__ x, int project) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < S.nt; t += gridDim.x * blockDim.x) {
     int v[4];
     d3 X[4];
     load_tet(S, x, t, v, X);
-    const double* Mi = S.Dm_inv + 9 * (int64_t)t;
-    double F[3][3];
-    def_grad(X, Mi, F);
-    const double mu = S.mu[t], lam = S.lam[t], vol = S.vol[t];
-    double U[3][3], s[3], V[3][3];
-    svd3(F, U, s, V);
-    const double lnJ = log(s[0] * s[1] * s[2]);
-    const double c = mu - lam * lnJ;
+    const double* Md = S.Dm_inv + 9 * (int64_t)t;
+    T F[3][3], Mi[9];
+    def_grad_t<T>(X, Md, F);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Mi[k] = (T)Md[k];
+    const T mu = (T)S.mu[t], lam = (T)S.lam[t], vol = (T)S.vol[t];
+    T U[3][3], s[3], V[3][3];
+    svd3<T>(F, U, s, V);
+    const T lnJ = log(s[0] * s[1] * s[2]);
+    const T c = mu - lam * lnJ;
     // beta[b][m] = v_m . B_b  (B_b = row b-1 of Dm^{-1}, b = 1..3)
-    double beta[3][3];
+    T beta[3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int m = 0; m < 3; ++m)
         beta[b][m] = V[0][m] * Mi[3 * b] + V[1][m] * Mi[3 * b + 1] + V[2][m] * Mi[3 * b + 2];
-    double H[45];
+    T H[45];
 #pragma unroll
-    for (int k = 0; k < 45; ++k) H[k] = 0.0;
-    double w[9];
+    for (int k = 0; k < 45; ++k) H[k] = T(0);
+    T w[9];
     // scaling modes: eigen-decomposition of diag(mu + c/s^2) + lam (1/s)(1/s)^T
     {
-      double A[3][3], Q[3][3];
-      const double is[3] = {1.0 / s[0], 1.0 / s[1], 1.0 / s[2]};
+      T A[3][3], Q[3][3];
+      const T is[3] = {T(1) / s[0], T(1) / s[1], T(1) / s[2]};
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-          A[i][j] = lam * is[i] * is[j] + (i == j ? mu + c * is[i] * is[i] : 0.0);
-      jacobi3(A, Q);
+          A[i][j] = lam * is[i] * is[j] + (i == j ? mu + c * is[i] * is[i] : T(0));
+      jacobi3<T>(A, Q);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const double ev = A[k][k];
-        if (project && ev <= 0.0) continue;
+        const T ev = A[k][k];
+        if (project && ev <= T(0)) continue;
         // w[b][i] = sum_m U[i][m] q_m beta[b][m]
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          const double c0 = Q[0][k] * beta[b][0], c1 = Q[1][k] * beta[b][1], c2 = Q[2][k] * beta[b][2];
+          const T c0 = Q[0][k] * beta[b][0], c1 = Q[1][k] * beta[b][1], c2 = Q[2][k] * beta[b][2];
 #pragma unroll
           for (int i = 0; i < 3; ++i) w[3 * b + i] = U[i][0] * c0 + U[i][1] * c1 + U[i][2] * c2;
         }
-        rank1_45(H, w, ev);
+        rank1_45<T>(H, w, ev);
       }
     }
     // flip / twist modes of each singular-value pair
-    const double r2 = 0.70710678118654752440;
+    const T r2 = (T)0.70710678118654752440;
 #pragma unroll
     for (int pr = 0; pr < 3; ++pr) {
       const int i = pr == 2 ? 1 : 0;
       const int j = pr == 0 ? 1 : 2;
-      const double q = c / (s[i] * s[j]);
+      const T q = c / (s[i] * s[j]);
 #pragma unroll
       for (int sgn = 0; sgn < 2; ++sgn) {
-        const double ev = sgn == 0 ? mu + q : mu - q;   // flip : twist
-        if (project && ev <= 0.0) continue;
-        const double sg = sgn == 0 ? 1.0 : -1.0;
+        const T ev = sgn == 0 ? mu + q : mu - q;   // flip : twist
+        if (project && ev <= T(0)) continue;
+        const T sg = sgn == 0 ? T(1) : T(-1);
         // D = U (E_ij +- E_ji) V^T / sqrt2 ; w[b] = (u_i beta_bj +- u_j beta_bi)/sqrt2
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-          const double ci = r2 * beta[b][j], cj = sg * r2 * beta[b][i];
+          const T ci = r2 * beta[b][j], cj = sg * r2 * beta[b][i];
 #pragma unroll
           for (int k = 0; k < 3; ++k) w[3 * b + k] = U[k][i] * ci + U[k][j] * cj;
         }
-        rank1_45(H, w, ev);
+        rank1_45<T>(H, w, ev);
       }
     }
     // blocks of vertices 1..3, scaled by the rest volume
@@ -303,7 +348,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) blk[a][b][i][k] = vol * h45(H, 3 * (a - 1) + i, 3 * (b - 1) + k);
+          for (int k = 0; k < 3; ++k) blk[a][b][i][k] = (double)(vol * h45<T>(H, 3 * (a - 1) + i, 3 * (b - 1) + k));
     // translation invariance: H[a][0] = -sum_b H[a][b], H[0][0] = sum_ab H[a][b]
 #pragma unroll
     for (int a = 1; a < 4; ++a)
@@ -450,7 +495,11 @@ bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st) {
   BAL_LAUNCH_CHECK();
   if (S.d.nnzL > 0) BAL_CUDA(cudaMemsetAsync(S.d.Lval, 0, sizeof(double) * 9 * S.d.nnzL, st));
   if (S.d.nt > 0) {
-    k_elastic_hess<<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, S.project ? 1 : 0);
+    // single-precision path: element eigensystems in FP32 (projected Hessian only)
+    if (S.prm.precision == BAL_PREC_FP32 && S.project)
+      k_elastic_hess<float><<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, 1);
+    else
+      k_elastic_hess<double><<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, S.project ? 1 : 0);
     ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }

@@ -886,7 +886,7 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     info->warm_iters = 0;
     info->n_groups = 0;
     info->negative_curvature = 0;
-    info->precision_used = BAL_PREC_MIXED;
+    info->precision_used = S.prm.precision == BAL_PREC_FP32 ? BAL_PREC_FP32 : BAL_PREC_MIXED;
   }
   return BAL_OK;
 }
@@ -1003,7 +1003,7 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
     }
     return BAL_OK;
   }
-  if (S.prm.precision == BAL_PREC_MIXED) {
+  if (S.prm.precision == BAL_PREC_MIXED || S.prm.precision == BAL_PREC_FP32) {
     BAL_TRY(pcg_mixed(S, b, x, tol, max_it, info, st));
     if (info) {
       info->warm_iters = witers;
