@@ -14,13 +14,18 @@
 // as a gather, one thread per row, with no atomics, so the result is
 // deterministic. The static lower blocks sit in a sliced-ELL layout: 32 rows
 // per slice, entry k of the 32 rows adjacent in memory and the 9 entries of a
-// block 32 values apart, so one warp reads a slice with coalesced loads. Row i
+// block 32 values apart, so one warp reads a slice with coalesced loads. Rows
+// are given to slice lanes after a stable sort by list length within windows
+// of 4096 rows (sliced ELL with a sorting window), which removes most of the
+// padding that the alternating neighbour counts of a Kuhn-split lattice leave
+// in 32 consecutive rows while keeping each slice's rows close in index. Row i
 // sums D_i v_i, its own blocks L_ij v_j, then the transposes L_ki^T v_k of the
 // blocks stored in later rows k with column i (the column-side list holds their
 // value positions); on a lattice ordering those also lie side by side for 32
 // adjacent rows, and their second read is served by L2. Contact blocks are
 // added by a second kernel over the rows they touch.
 #include <cub/cub.cuh>
+#include <algorithm>
 #include <utility>
 
 #include "dd.cuh"
@@ -36,6 +41,8 @@ constexpr double kDdRange = 1e36;        // entries beyond this stay in the FP64
 // padding entries read zero blocks; spreading them over this many chunks keeps
 // every slice's padding reads on different L2 lines instead of one hot spot
 constexpr int kZeroChunks = 64;
+// rows are sorted by list length within windows of this many rows (128 slices)
+constexpr int kSellWindow = 4096;
 
 struct DDSys {
   const dd* D;            // [ns][9][32]
@@ -46,7 +53,8 @@ struct DDSys {
   const int32_t* offT;    // [ns+1]
   const int32_t* Tpos;    // [offT[ns]]
   const int32_t* Tsrc;    // [offT[ns]]
-  const short2* len;      // [ns*32] row-side and column-side list length of each row
+  const short2* len;      // [ns*32] row-side and column-side list length of each slot's row
+  const int32_t* srow;    // [ns*32] row of each slot (-1: none)
   int64_t zero;           // value position of the first chunk of zero blocks
   int nv, ns;
 };
@@ -86,14 +94,16 @@ __device__ __forceinline__ void dd3_acc(dd3& a, dd3 b) {
   a.z = dd_add(a.z, b.z);
 }
 
-// D or D^-1 (FP64, [nv][9]) into the slice-major double-float layout
-__global__ void k_dd_slices(int nv, const double* __restrict__ a, dd* __restrict__ out, unsigned int* bad) {
+// D or D^-1 (FP64, [nv][9]) into the slice-major double-float layout, block i
+// at slot slot_of[i] (slot i when slot_of is null)
+__global__ void k_dd_slices(int nv, const double* __restrict__ a, dd* __restrict__ out, unsigned int* bad,
+                            const int32_t* __restrict__ slot_of) {
   const int64_t n = 9 * (int64_t)nv;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / 9), e = (int)(t % 9);
     const double v = a[t];
     if (!(fabs(v) <= kDdRange)) atomicAdd(bad, 1u);
-    out[slice_base(i) + 32 * e] = dd_from(v);
+    out[slice_base(slot_of ? slot_of[i] : i) + 32 * e] = dd_from(v);
   }
 }
 // L values (FP64, CSR slot order [nL][9]) into their sliced positions
@@ -247,13 +257,14 @@ __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __res
   const int lane = threadIdx.x & 31;
   dd pq{0.f, 0.f};
   for (int s = blockIdx.x * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += gridDim.x * kDdWarps) {
-    const int i = 32 * s + lane;
-    const bool own = i < A.nv;
+    const int slot = 32 * s + lane;
+    const int i = A.srow[slot];
+    const bool own = i >= 0;
     const dd3 pi = own ? dd3_ld(p, i) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-    dd3 acc = mv_sliced(A.D + slice_base(i), pi);
+    dd3 acc = mv_sliced(A.D + slice_base(slot), pi);
     // lanes past their own row-side list length (padding) read a zero chunk,
     // which stays in L2; the column-side padding entries already point at one
-    const int lr = A.len[i].x;
+    const int lr = A.len[slot].x;
     const int r0 = A.offR[s], r1 = A.offR[s + 1];
 #pragma unroll 2
     for (int idx = r0 + lane; idx < r1; idx += 32) {
@@ -403,12 +414,32 @@ bal_status build_sell(Scene& S) {
         crow[e] = r;
       }
   }
+  // slot order: within each window of kSellWindow rows, rows sorted by
+  // row-side list length, then column-side length (descending, stable), so the
+  // 32 rows of a slice have near-equal lists and the slices carry little
+  // padding (on a Kuhn-split lattice the lower-neighbour counts alternate
+  // between 3 and 7 from one row to the next)
+  std::vector<int32_t> srow((size_t)ns * 32, -1), slot_of(nv);
+  for (int w0 = 0; w0 < nv; w0 += kSellWindow) {
+    const int w1 = std::min(nv, w0 + kSellWindow);
+    std::vector<int32_t> rows(w1 - w0);
+    for (int i = w0; i < w1; ++i) rows[i - w0] = i;
+    std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
+      const int la = rp[a + 1] - rp[a], lb = rp[b + 1] - rp[b];
+      if (la != lb) return la > lb;
+      return cp[a + 1] - cp[a] > cp[b + 1] - cp[b];
+    });
+    for (int k = 0; k < w1 - w0; ++k) {
+      srow[w0 + k] = rows[k];
+      slot_of[rows[k]] = w0 + k;
+    }
+  }
   std::vector<int32_t> offR(ns + 1, 0), offT(ns + 1, 0);
   for (int s = 0; s < ns; ++s) {
     int lr = 0, lt = 0;
     for (int l = 0; l < 32; ++l) {
-      const int i = 32 * s + l;
-      if (i >= nv) break;
+      const int i = srow[32 * s + l];
+      if (i < 0) break;
       lr = std::max(lr, rp[i + 1] - rp[i]);
       lt = std::max(lt, cp[i + 1] - cp[i]);
     }
@@ -427,8 +458,8 @@ bal_status build_sell(Scene& S) {
   for (int s = 0; s < ns; ++s) {
     const int lr = (offR[s + 1] - offR[s]) / 32;
     for (int l = 0; l < 32; ++l) {
-      const int i = 32 * s + l;
-      const int len = i < nv ? rp[i + 1] - rp[i] : 0;
+      const int i = srow[32 * s + l];
+      const int len = i >= 0 ? rp[i + 1] - rp[i] : 0;
       for (int k = 0; k < lr; ++k) {
         const int32_t idx = offR[s] + 32 * k + l;
         if (k < len) {
@@ -436,7 +467,7 @@ bal_status build_sell(Scene& S) {
           Rcol[idx] = col[slot];
           pos[slot] = 9 * (idx - l) + l;
         } else {
-          Rcol[idx] = i < nv ? i : 0;   // padding: a zero block times a valid entry
+          Rcol[idx] = i >= 0 ? i : 0;   // padding: a zero block times a valid entry
         }
       }
     }
@@ -444,8 +475,8 @@ bal_status build_sell(Scene& S) {
   for (int s = 0; s < ns; ++s) {
     const int lt = (offT[s + 1] - offT[s]) / 32;
     for (int l = 0; l < 32; ++l) {
-      const int i = 32 * s + l;
-      const int len = i < nv ? cp[i + 1] - cp[i] : 0;
+      const int i = srow[32 * s + l];
+      const int len = i >= 0 ? cp[i + 1] - cp[i] : 0;
       for (int k = 0; k < lt; ++k) {
         const int32_t idx = offT[s] + 32 * k + l;
         if (k < len) {
@@ -453,7 +484,7 @@ bal_status build_sell(Scene& S) {
           Tsrc[idx] = crow[cp[i] + k];
         } else {
           Tpos[idx] = zero + 288 * (s % kZeroChunks) + l;   // padding: a zero chunk
-          Tsrc[idx] = i < nv ? i : 0;
+          Tsrc[idx] = i >= 0 ? i : 0;
         }
       }
     }
@@ -465,7 +496,7 @@ bal_status build_sell(Scene& S) {
       set_error("df64 pcg: vertex %d has more than 32767 neighbours", i);
       return BAL_ERR_CAPACITY;
     }
-    len[i] = short2{(short)a, (short)b};
+    len[slot_of[i]] = short2{(short)a, (short)b};
   }
   BAL_TRY(buf_reserve(S.sell_len, sizeof(short2) * len.size()));
   BAL_CUDA(cudaMemcpy(S.sell_len.p, len.data(), sizeof(short2) * len.size(), cudaMemcpyHostToDevice));
@@ -480,6 +511,8 @@ bal_status build_sell(Scene& S) {
   BAL_TRY(up(S.sell_Tpos, Tpos));
   BAL_TRY(up(S.sell_Tsrc, Tsrc));
   BAL_TRY(up(S.sell_pos, pos));
+  BAL_TRY(up(S.sell_srow, srow));
+  BAL_TRY(up(S.sell_slot, slot_of));
   const size_t nRval = 9 * (size_t)(nR + 32 * kZeroChunks), nDval = (size_t)ns * 9 * 32;
   BAL_TRY(buf_reserve(S.dd_R, sizeof(dd) * nRval));
   BAL_TRY(buf_reserve(S.dd_D, sizeof(dd) * nDval));
@@ -550,9 +583,10 @@ bal_status refresh_dd(Scene& S, bool* in_range, cudaStream_t st) {
   if (!S.sell_built) BAL_TRY(build_sell(S));
   unsigned int* bad = reinterpret_cast<unsigned int*>(S.scal + 61);
   BAL_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
-  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.D, S.dd_D.as<dd>(), bad);
+  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.D, S.dd_D.as<dd>(), bad,
+                                                               S.sell_slot.as<int32_t>());
   ::bal::note_launch();
-  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.Dinv, S.dd_Dinv.as<dd>(), bad);
+  k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.Dinv, S.dd_Dinv.as<dd>(), bad, nullptr);
   ::bal::note_launch();
   if (nL) {
     k_dd_scatter<<<grid_for(9 * nL), kThreads, 0, st>>>(nL, S.d.Lval, S.sell_pos.as<int32_t>(),
@@ -601,6 +635,7 @@ DDSys dd_sys(Scene& S) {
   A.Tpos = S.sell_Tpos.as<int32_t>();
   A.Tsrc = S.sell_Tsrc.as<int32_t>();
   A.len = S.sell_len.as<short2>();
+  A.srow = S.sell_srow.as<int32_t>();
   A.zero = S.sell_zero;
   A.nv = S.d.nv;
   A.ns = S.n_slices;

@@ -93,7 +93,9 @@ struct Scene {
   Buf sell_Rcol;              // [offR[n]] column of each row-side entry
   Buf sell_Tpos, sell_Tsrc;   // [offT[n]] value position / source row of each column-side entry
   Buf sell_pos;               // [nnzL] value position of each CSR slot
-  Buf sell_len;               // [n_slices*32] short2: row-side, column-side list length per row
+  Buf sell_len;               // [n_slices*32] short2: row-side, column-side list length per slot
+  Buf sell_srow, sell_slot;   // slot -> row (-1: none) and row -> slot: rows sorted by list length
+                              // within windows of 4096 (sliced ELL with a sorting window)
   int64_t sell_zero = 0;      // value position of the chunk of zero blocks (padding)
   // double-float values (valid after the refresh in pcg_df64): slice-major D,
   // D^-1 ([n_slices][9][32]), the sliced lower blocks, contact blocks [nnzC][9],
