@@ -257,11 +257,12 @@ __global__ void k_assemble_init(Dev S) {
   }
 }
 
-__device__ inline void add_block(double* dst, const double blk[3][3], bool transpose) {
+template <typename T>
+__device__ inline void add_block(double* dst, const T blk[3][3], bool transpose) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, transpose ? blk[k][i] : blk[i][k]);
+    for (int k = 0; k < 3; ++k) atomicAdd(dst + 3 * i + k, (double)(transpose ? blk[k][i] : blk[i][k]));
 }
 
 // Element stencil Hessians in arithmetic T (double: the FP64 path; float: the
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
       }
     }
     // blocks of vertices 1..3, scaled by the rest volume
-    double blk[4][4][3][3];
+    T blk[4][4][3][3];
 #pragma unroll
     for (int a = 1; a < 4; ++a)
 #pragma unroll
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) blk[a][b][i][k] = (double)(vol * h45<T>(H, 3 * (a - 1) + i, 3 * (b - 1) + k));
+          for (int k = 0; k < 3; ++k) blk[a][b][i][k] = vol * h45<T>(H, 3 * (a - 1) + i, 3 * (b - 1) + k);
     // translation invariance: H[a][0] = -sum_b H[a][b], H[0][0] = sum_ab H[a][b]
 #pragma unroll
     for (int a = 1; a < 4; ++a)
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const double sum = blk[a][1][i][k] + blk[a][2][i][k] + blk[a][3][i][k];
+          const T sum = blk[a][1][i][k] + blk[a][2][i][k] + blk[a][3][i][k];
           blk[a][0][i][k] = -sum;
           blk[0][a][k][i] = -sum;
         }
@@ -364,11 +365,20 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k) blk[0][0][i][k] = -(blk[1][0][i][k] + blk[2][0][i][k] + blk[3][0][i][k]);
-    // Lambda: mean eigenvalue of the projected element stencil = trace / 12
-    double tr = 0.0;
+    // the two summation orders of H[0][0] round differently: keep the block symmetric
 #pragma unroll
-    for (int a = 0; a < 4; ++a) tr += blk[a][a][0][0] + blk[a][a][1][1] + blk[a][a][2][2];
-    tr *= (1.0 / 12.0);
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = i + 1; k < 3; ++k) {
+        const T m = T(0.5) * (blk[0][0][i][k] + blk[0][0][k][i]);
+        blk[0][0][i][k] = m;
+        blk[0][0][k][i] = m;
+      }
+    // Lambda: mean eigenvalue of the projected element stencil = trace / 12
+    T trT = T(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) trT += blk[a][a][0][0] + blk[a][a][1][1] + blk[a][a][2][2];
+    const double tr = (double)trT * (1.0 / 12.0);
     bool pin[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
       atomicAdd(S.Lambda + 3 * v[a], tr);
       atomicAdd(S.Lambda + 3 * v[a] + 1, tr);
       atomicAdd(S.Lambda + 3 * v[a] + 2, tr);
-      if (!pin[a]) add_block(S.D + 9 * (int64_t)v[a], blk[a][a], false);
+      if (!pin[a]) add_block<T>(S.D + 9 * (int64_t)v[a], blk[a][a], false);
     }
     const int pa[6] = {1, 2, 3, 2, 3, 3};
     const int pb[6] = {0, 0, 0, 1, 1, 2};
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(128) k_elastic_hess(Dev S, const double* __res
       const int a = pa[k], b = pb[k];
       if (pin[a] || pin[b]) continue;
       const int code = slots[k];
-      add_block(S.Lval + 9 * (int64_t)(code >> 1), blk[a][b], (code & 1) != 0);
+      add_block<T>(S.Lval + 9 * (int64_t)(code >> 1), blk[a][b], (code & 1) != 0);
     }
   }
 }
