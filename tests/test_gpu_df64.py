@@ -97,6 +97,51 @@ def _block_jacobi_cg(H, b, iters):
     return x
 
 
+def _diag_block_inverses(H, n):
+    C = H.tocoo()
+    keep = (C.row // 3) == (C.col // 3)
+    B = np.zeros((n, 3, 3))
+    np.add.at(B, (C.row[keep] // 3, C.row[keep] % 3, C.col[keep] % 3), C.data[keep])
+    return np.linalg.inv(B)
+
+
+def test_df64_iterates_across_sorting_windows():
+    """5,488 vertices: two windows of the slot sort (4,096 + a ragged 1,392)
+    and a ragged last slice; three df64 PCG iterates against textbook
+    block-Jacobi CG on the oracle's Hessian."""
+    sc = scenes.cube_stack(n_cubes=2, n=13)
+    assert sc.n_verts > 4096 and sc.n_verts % 4096 != 0 and sc.n_verts % 32 != 0
+    rng = np.random.default_rng(14)
+    x = sc.X + 2e-4 * rng.normal(size=sc.X.shape) * (sc.pinned == 0)[:, None]
+    S = bal.Scene(sc, bal.default_params(precision=bal.PREC_DF64, pcg_stall_window=0))
+    S.step_begin(T(sc.X), T(sc.V0))
+    S.set_al_state(3.0, 3.0)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    S.assemble_hessian(T(x), g)
+    m, y, ps = oracle_state(sc, x, 3.0)
+    H = system.hessian(m, x, y, ps, 3.0).tocsr()
+    n = sc.n_verts
+    Dinv = _diag_block_inverses(H, n)
+    prec = lambda r: np.einsum("nij,nj->ni", Dinv, r.reshape(n, 3)).ravel()  # noqa: E731
+    b = -g.cpu().numpy()
+    xr, r = np.zeros_like(b), b.copy()
+    z = prec(r)
+    p, rz = z.copy(), r @ z
+    for _ in range(3):
+        q = H @ p
+        a = rz / (p @ q)
+        xr += a * p
+        r -= a * q
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    sol = torch.zeros_like(g)
+    info = S.pcg_solve(-g, sol, 1e-30, 3)
+    assert info["iters"] == 3 and info["precision_used"] == bal.PREC_DF64
+    assert np.abs(sol.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
+
+
 @pytest.mark.parametrize("iters", [1, 2, 5])
 def test_df64_iterates_match_textbook_cg_on_oracle_hessian(multi_tile_case, iters):
     sc, S, x, b, H, m, y = multi_tile_case
