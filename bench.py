@@ -301,6 +301,21 @@ def run_precision_sweep(args):
             "data": "synthetic (seeded procedural scene)"}
 
 
+def reduce_over_ranks(ms, e2e_ms, pcg_iters, e2e_iters, world, dev=None):
+    """Whole-job figures of a replicas-only run: the slowest rank's times (max)
+    and the PCG iterations of all ranks (sum). One collective per figure kind,
+    outside the timed region; identity for a single process."""
+    if world <= 1:
+        return ms, e2e_ms, pcg_iters, e2e_iters
+    import torch
+    t = torch.tensor([ms, e2e_ms, float(pcg_iters), float(e2e_iters)], dtype=torch.float64, device=dev)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[2]), float(sm[3])
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2407_00046_b300 import bal, build, scenes
@@ -400,16 +415,7 @@ def run_ours(args, rank, world):
     pcg_only = pi["iters"] / (time.perf_counter() - p0)
     forms = precision_forms(S, sc, dev, args) if not args.no_forms else None
 
-    # max over ranks
-    vals = torch.tensor([ms, e2e_ms, float(pcg_iters), float(e2e_iters)], dtype=torch.float64)
-    if world > 1:
-        t = vals.to(dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        ms, e2e_ms = float(mx[0]), float(mx[1])
-        pcg_iters, e2e_iters = float(sm[2]), float(sm[3])
+    ms, e2e_ms, pcg_iters, e2e_iters = reduce_over_ranks(ms, e2e_ms, pcg_iters, e2e_iters, world, dev)
     if rank != 0:
         return None
     value = pcg_iters / (ms * 1e-3)
