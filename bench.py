@@ -183,6 +183,13 @@ def run_pcg_only(args):
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
     v = torch.tensor(sc.V0, dtype=torch.float64, device=dev)
+    warm_steps = getattr(args, "pcg_warm_steps", 0)
+    if warm_steps > 0:
+        # reach a state in contact first: time steps with the bench's solver settings
+        S.set_params(_scene_params(args, bal))
+        for _ in range(warm_steps):
+            S.time_step(x, v, check=False)
+        S.set_params(params)
     S.step_begin(x, v)
     g = torch.empty_like(x)
     view = S.assemble_hessian(x, g)
@@ -206,7 +213,8 @@ def run_pcg_only(args):
     kms = k_ms / max(k_n, 1)
     return {"mode": "pcg", "scene": args.scene, "precision": args.precision,
             "iters_per_solve": args.pcg_iters, "ms_per_iter": round(ms, 4),
-            "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "n_verts": sc.n_verts,
+            "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "nnz_C": view["nnz_C"],
+            "warm_steps": warm_steps, "n_verts": sc.n_verts,
             "spmv_kernel": kname, "spmv_ms_per_launch": round(kms, 5),
             "spmv_gbs": round(byts / (kms * 1e-3) / 1e9, 1), "spmv_bytes": byts}
 
@@ -615,6 +623,8 @@ def main():
                          "precision-sweep: the same steps in FP64, df64 and FP32 + refinement")
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--pcg-iters", type=int, default=200)
+    ap.add_argument("--pcg-warm-steps", type=int, default=0,
+                    help="--mode pcg: time steps taken before the assembly (a state in contact)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))

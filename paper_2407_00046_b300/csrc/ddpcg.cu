@@ -23,7 +23,8 @@
 // blocks stored in later rows k with column i (the column-side list holds their
 // value positions); on a lattice ordering those also lie side by side for 32
 // adjacent rows, and their second read is served by L2. Contact blocks are
-// added by a second kernel over the rows they touch.
+// applied by extra CTAs of the same launch, eight lanes per contact row, into
+// a per-contact-row buffer that the update kernel adds to those rows.
 #include <cub/cub.cuh>
 #include <algorithm>
 #include <utility>
@@ -43,6 +44,8 @@ constexpr double kDdRange = 1e36;        // entries beyond this stay in the FP64
 constexpr int kZeroChunks = 64;
 // rows are sorted by list length within windows of this many rows (128 slices)
 constexpr int kSellWindow = 4096;
+// lanes that share one contact row in the contact CTAs of k_dd_spmv
+constexpr int kContactLanes = 8;
 
 struct DDSys {
   const dd* D;            // [ns][9][32]
@@ -147,6 +150,14 @@ __global__ void k_crow_src(const int32_t* __restrict__ ent, const int32_t* __res
   if (blockIdx.x == 0 && threadIdx.x == 0) ptr[*nrows] = n2;
 }
 
+// crow_of[rows[c]] = c for the *nrows unique contact rows
+__global__ void k_crow_of(const int32_t* __restrict__ rows, int n2, const int32_t* __restrict__ nrows,
+                          int32_t* __restrict__ crow_of) {
+  const int n = *nrows;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n && c < n2; c += gridDim.x * blockDim.x)
+    crow_of[rows[c]] = c;
+}
+
 // Programmatic dependent launch: a PCG-loop kernel lets the next one in the
 // stream be scheduled at once, and waits for the previous grid to complete
 // (and its writes to be visible) before it reads anything that grid produced.
@@ -245,82 +256,95 @@ __global__ void __launch_bounds__(NT) k_dd_dir(int nv, const dd* __restrict__ z,
   }
 }
 
-// q = (D + L + L^T) p, one warp per slice; partial sums of p^T q. With
-// finalize, the last CTA sets alpha = rz / p^T q (no contact blocks). Padding
-// entries read L2-resident zero chunks, so every lane runs the same loads
-// without a branch and padding costs no DRAM traffic.
-__global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, const dd* __restrict__ p,
-                                                        dd* __restrict__ q, PcgScalars* P,
-                                                        double* partials, int finalize) {
+// Contact part of H p for contact rows b, b + nb, ... (CTAs of the SpMV grid
+// past the slice CTAs): qc_t = sum of the contact blocks of row rows[t], both
+// orientations, applied to p. G lanes share a row: lane j of the group takes
+// entries j, j + G, ... and the group's sums are combined by shuffles in a
+// fixed order (deterministic). Each warp covers 32 / G consecutive rows and
+// iterates while any of them exists, so every lane reaches the shuffles.
+// Returns this thread's share of sum_t p_rows[t] . qc_t.
+template <int G>
+__device__ dd contact_rows(const DDContact& Cr, const dd* __restrict__ p, dd* __restrict__ qc, int b, int nb) {
+  static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G is a power of two <= 32");
+  constexpr int kRowsPerWarp = 32 / G;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  const int64_t warp = (b * (int64_t)kDdThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)nb * kDdThreads) >> 5;
+  dd pq{0.f, 0.f};
+  for (int64_t t0 = warp * kRowsPerWarp; t0 < Cr.n; t0 += nwarps * kRowsPerWarp) {
+    const int64_t t = t0 + lane / G;
+    const bool valid = t < Cr.n;
+    dd3 acc{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+    if (valid) {
+      const int e1 = Cr.ptr[t + 1];
+      for (int e = Cr.ptr[t] + sub; e < e1; e += G) {
+        const int ent = Cr.ent[e];
+        const dd* B = Cr.C + 9 * (int64_t)(ent >> 1);
+        const dd3 v = dd3_ld(p, Cr.src[e]);
+        dd3_acc(acc, (ent & 1) ? dd3_mtv(B, v) : dd3_mv(B, v));
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+      dd3 o;
+      o.x = dd{__shfl_xor_sync(0xffffffffu, acc.x.hi, off), __shfl_xor_sync(0xffffffffu, acc.x.lo, off)};
+      o.y = dd{__shfl_xor_sync(0xffffffffu, acc.y.hi, off), __shfl_xor_sync(0xffffffffu, acc.y.lo, off)};
+      o.z = dd{__shfl_xor_sync(0xffffffffu, acc.z.hi, off), __shfl_xor_sync(0xffffffffu, acc.z.lo, off)};
+      dd3_acc(acc, o);
+    }
+    if (valid && sub == 0) {
+      dd3_st(qc, (int)t, acc);
+      pq = dd_add(pq, dd3_dot(dd3_ld(p, Cr.rows[t]), acc));
+    }
+  }
+  return pq;
+}
+
+// q = (D + L + L^T) p over the slices (CTAs [0, n_row_ctas)) and the contact
+// part per contact row into qc (the CTAs after them; placing them first
+// measured 2% slower); partial sums of p . Hp; the last CTA to finish sets
+// alpha.
+__global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, DDContact Cr, int n_row_ctas,
+                                                        const dd* __restrict__ p, dd* __restrict__ q,
+                                                        dd* __restrict__ qc, PcgScalars* P,
+                                                        double* partials) {
   pdl_enter();
   if (P->done) return;
   const int lane = threadIdx.x & 31;
   dd pq{0.f, 0.f};
-  for (int s = blockIdx.x * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += gridDim.x * kDdWarps) {
-    const int slot = 32 * s + lane;
-    const int i = A.srow[slot];
-    const bool own = i >= 0;
-    const dd3 pi = own ? dd3_ld(p, i) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-    dd3 acc = mv_sliced(A.D + slice_base(slot), pi);
-    // lanes past their own row-side list length (padding) read a zero chunk,
-    // which stays in L2; the column-side padding entries already point at one
-    const int lr = A.len[slot].x;
-    const int r0 = A.offR[s], r1 = A.offR[s + 1];
+  if ((int)blockIdx.x >= n_row_ctas) {
+    pq = contact_rows<kContactLanes>(Cr, p, qc, blockIdx.x - n_row_ctas, gridDim.x - n_row_ctas);
+  } else {
+    for (int s = blockIdx.x * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += n_row_ctas * kDdWarps) {
+      const int slot = 32 * s + lane;
+      const int i = A.srow[slot];
+      const bool own = i >= 0;
+      const dd3 pi = own ? dd3_ld(p, i) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+      dd3 acc = mv_sliced(A.D + slice_base(slot), pi);
+      // lanes past their own row-side list length (padding) read a zero chunk,
+      // which stays in L2; the column-side padding entries already point at one
+      const int lr = A.len[slot].x;
+      const int r0 = A.offR[s], r1 = A.offR[s + 1];
 #pragma unroll 2
-    for (int idx = r0 + lane; idx < r1; idx += 32) {
-      const int64_t vb = idx - r0 < 32 * lr ? 9 * (int64_t)(idx - lane) + lane
-                                            : A.zero + 288 * (s % kZeroChunks) + lane;
-      dd3_acc(acc, mv_sliced(A.R + vb, dd3_ld(p, A.Rcol[idx])));
-    }
-    const int t1 = A.offT[s + 1];
+      for (int idx = r0 + lane; idx < r1; idx += 32) {
+        const int64_t vb = idx - r0 < 32 * lr ? 9 * (int64_t)(idx - lane) + lane
+                                              : A.zero + 288 * (s % kZeroChunks) + lane;
+        dd3_acc(acc, mv_sliced(A.R + vb, dd3_ld(p, A.Rcol[idx])));
+      }
+      const int t1 = A.offT[s + 1];
 #pragma unroll 2
-    for (int idx = A.offT[s] + lane; idx < t1; idx += 32)
-      dd3_acc(acc, mtv_sliced(A.R + A.Tpos[idx], dd3_ld(p, A.Tsrc[idx])));
-    if (own) {
-      dd3_st(q, i, acc);
-      pq = dd_add(pq, dd3_dot(pi, acc));
+      for (int idx = A.offT[s] + lane; idx < t1; idx += 32)
+        dd3_acc(acc, mtv_sliced(A.R + A.Tpos[idx], dd3_ld(p, A.Tsrc[idx])));
+      if (own) {
+        dd3_st(q, i, acc);
+        pq = dd_add(pq, dd3_dot(pi, acc));
+      }
     }
   }
   pq = dd_block_sum<kDdThreads>(pq);
   if (threadIdx.x == 0) partials[blockIdx.x] = dd_to(pq);
-  if (!finalize) return;
   if (dd_arrive_last(&P->counter)) {
     const double tpq = dd_sum_partials<kDdThreads>(partials, gridDim.x);
-    if (threadIdx.x == 0) {
-      set_alpha(P, tpq);
-      P->counter = 0;
-    }
-  }
-}
-
-// q_i += sum of the contact blocks of row i (both orientations) applied to p;
-// partial sums of p_i . (contact part of q_i); the last CTA adds the n_prev
-// partials of k_dd_spmv and sets alpha.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_dd_contact(DDContact Cr, const dd* __restrict__ p,
-                                                   dd* __restrict__ q, PcgScalars* P, double* partials,
-                                                   int n_prev) {
-  pdl_enter();
-  if (P->done) return;
-  dd pq{0.f, 0.f};
-  for (int t = blockIdx.x * NT + threadIdx.x; t < Cr.n; t += gridDim.x * NT) {
-    const int i = Cr.rows[t];
-    dd3 acc{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-    for (int e = Cr.ptr[t]; e < Cr.ptr[t + 1]; ++e) {
-      const int ent = Cr.ent[e];
-      const dd* B = Cr.C + 9 * (int64_t)(ent >> 1);
-      const dd3 v = dd3_ld(p, Cr.src[e]);
-      dd3_acc(acc, (ent & 1) ? dd3_mtv(B, v) : dd3_mv(B, v));
-    }
-    dd3 qi = dd3_ld(q, i);
-    dd3_acc(qi, acc);
-    dd3_st(q, i, qi);
-    pq = dd_add(pq, dd3_dot(dd3_ld(p, i), acc));
-  }
-  pq = dd_block_sum<NT>(pq);
-  if (threadIdx.x == 0) partials[n_prev + blockIdx.x] = dd_to(pq);
-  if (dd_arrive_last(&P->counter)) {
-    const double tpq = dd_sum_partials<NT>(partials, n_prev + gridDim.x);
     if (threadIdx.x == 0) {
       set_alpha(P, tpq);
       P->counter = 0;
@@ -331,7 +355,8 @@ __global__ void __launch_bounds__(NT) k_dd_contact(DDContact Cr, const dd* __res
 // x += alpha p, r -= alpha q, z = D^{-1} r; rz, ||r||; convergence, stagnation, beta
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, const dd* __restrict__ p,
-                                                  const dd* __restrict__ q, dd* __restrict__ r,
+                                                  const dd* __restrict__ q, const int32_t* __restrict__ crow_of,
+                                                  const dd* __restrict__ qc, dd* __restrict__ r,
                                                   dd* __restrict__ z, PcgScalars* P, double* partials) {
   pdl_enter();
   if (P->done) return;
@@ -340,7 +365,12 @@ __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, c
   dd rz{0.f, 0.f}, rr{0.f, 0.f};
   for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
     dd3_st(x, i, dd3_axpy(alpha, dd3_ld(p, i), dd3_ld(x, i)));
-    const dd3 ri = dd3_axpy(malpha, dd3_ld(q, i), dd3_ld(r, i));
+    dd3 qi = dd3_ld(q, i);
+    if (crow_of) {   // H p of a contact row: slice part + contact part
+      const int c = crow_of[i];
+      if (c >= 0) dd3_acc(qi, dd3_ld(qc, c));
+    }
+    const dd3 ri = dd3_axpy(malpha, qi, dd3_ld(r, i));
     const dd3 zi = dinv_apply(A, i, ri);
     dd3_st(r, i, ri);
     dd3_st(z, i, zi);
@@ -568,6 +598,13 @@ bal_status build_contact_rows(Scene& S, cudaStream_t st) {
                                                 S.cr_ptr.as<int32_t>());
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
+  // vertex -> contact row, and room for the contact part of H p per contact row
+  BAL_TRY(buf_reserve(S.cr_of, sizeof(int32_t) * (size_t)S.d.nv));
+  BAL_TRY(buf_reserve(S.cr_q, sizeof(dd) * 3 * (size_t)n2));
+  BAL_CUDA(cudaMemsetAsync(S.cr_of.p, 0xff, sizeof(int32_t) * (size_t)S.d.nv, st));   // -1
+  k_crow_of<<<grid_for(n2), kThreads, 0, st>>>(S.cr_rows.as<int32_t>(), n2, num, S.cr_of.as<int32_t>());
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
   int32_t n = 0;
   BAL_CUDA(cudaMemcpyAsync(&n, num, sizeof(n), cudaMemcpyDeviceToHost, st));
   BAL_CUDA(cudaStreamSynchronize(st));
@@ -680,8 +717,12 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
   dd *ex = V, *er = V + n3, *ez = V + 2 * n3, *ep = V + 3 * n3, *eq = V + 4 * n3;
   const int gs = std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
   const int gv = std::min((nv + kDdThreads - 1) / kDdThreads, kMaxPartials / 2);   // one vertex per thread
-  const int gc = std::max(1, std::min((Cr.n + kDdThreads - 1) / kDdThreads, kMaxPartials / 2));
-  const bool has_c = Cr.n > 0;
+  // contact CTAs appended to the SpMV grid (none without contact)
+  const int gc = Cr.n > 0 ? std::max(1, std::min((int)(((int64_t)Cr.n * kContactLanes + kDdThreads - 1) /
+                                                       kDdThreads), kMaxPartials / 2))
+                          : 0;
+  const int32_t* crow_of = Cr.n > 0 ? S.cr_of.as<int32_t>() : nullptr;
+  dd* eqc = S.cr_q.as<dd>();
   double rn, bn;
   BAL_TRY(residual_fp64(S, b, x, S.pcg_r, &rn, &bn, st));
   const double r0 = rn;
@@ -714,20 +755,15 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
         // one SpMV per chunk is timed: an event between two launches ends
         // their programmatic overlap
         if (k == 0) kt_before(S, 0, st);
-        BAL_CUDA(launch_pdl(k_dd_spmv, gs, kDdThreads, st, A, (const dd*)ep, eq, S.pcg, S.partials,
-                            has_c ? 0 : 1));
+        BAL_CUDA(launch_pdl(k_dd_spmv, gs + gc, kDdThreads, st, A, Cr, gs, (const dd*)ep, eq, eqc, S.pcg,
+                            S.partials));
         if (k == 0) {
           kt_after(S, 0, st);
           ++timed;
         }
         ::bal::note_launch();
-        if (has_c) {
-          BAL_CUDA(launch_pdl(k_dd_contact<kDdThreads>, gc, kDdThreads, st, Cr, (const dd*)ep, eq, S.pcg,
-                              S.partials, gs));
-          ::bal::note_launch();
-        }
         BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, gv, kDdThreads, st, A, ex, (const dd*)ep,
-                            (const dd*)eq, er, ez, S.pcg, S.partials));
+                            (const dd*)eq, crow_of, (const dd*)eqc, er, ez, S.pcg, S.partials));
         ::bal::note_launch();
       }
       BAL_LAUNCH_CHECK();

@@ -106,6 +106,7 @@ struct Scene {
   // (2c + transposed) and source vertices in CSR form
   int32_t n_crows = 0;
   Buf cr_rows, cr_ptr, cr_ent, cr_src, cr_key, cr_key_alt, cr_val, cr_val_alt, cr_cnt, cr_num;
+  Buf cr_of, cr_q;               // vertex -> contact row (-1: none); contact part of H p per contact row
   bool assembled = false;
   bool project = true;           // PSD projection of stencil Hessians (false: adjoint)
   double* E = nullptr;           // [nt] Young's modulus (device)
