@@ -4,7 +4,7 @@ gravity), ten steps, Newton tolerance 1e-8: positions and velocities after each
 step, Newton iterations and convergence flags. Calls only oracle/ (the FP64 CPU
 reference with dense Cholesky solves).
 
-    python tests/golden/make_cfg1_two_cubes.py   # ~10 min on one core
+    python tests/golden/make_two_cubes_trajectory.py   # ~10 min on one core
 """
 import os
 import sys
@@ -36,7 +36,7 @@ def main():
         conv.append(bool(info["converged"]))
         nA.append(len(keys))
         print(k, info["iters"], info["converged"], len(keys), flush=True)
-    out = os.path.join(os.path.dirname(__file__), "cfg1_two_cubes.npz")
+    out = os.path.join(os.path.dirname(__file__), "two_cubes_trajectory.npz")
     np.savez_compressed(out, x=np.array(xs), v=np.array(vs), newton_iters=np.array(iters),
                         converged=np.array(conv), n_active=np.array(nA), newton_tol=NEWTON_TOL,
                         newton_max=NEWTON_MAX)

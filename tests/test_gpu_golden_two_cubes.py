@@ -1,6 +1,6 @@
 """The two-cube workload (two 7^3-cell Neo-Hookean cubes, 4,116 tets, 1 cm
 gap, E = 1e5, ten steps) through the C ABI against the oracle's trajectory,
-stored by tests/golden/make_cfg1_two_cubes.py (FP64 CPU, dense Cholesky
+stored by tests/golden/make_two_cubes_trajectory.py (FP64 CPU, dense Cholesky
 solves): positions after every step while the oracle's steps converge."""
 import os
 
@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 
 from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 
-GOLD = os.path.join(os.path.dirname(__file__), "golden", "cfg1_two_cubes.npz")
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "two_cubes_trajectory.npz")
 
 
-def test_cfg1_trajectory_matches_the_oracle_golden_file():
+def test_two_cubes_trajectory_matches_the_oracle_golden_file():
     g = np.load(GOLD)
     sc = scenes.two_cubes()
     S = bal.Scene(sc, bal.default_params(newton_tol=float(g["newton_tol"]), newton_max_iter=int(g["newton_max"]),
