@@ -363,6 +363,8 @@ __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, c
   const dd alpha{P->alpha_hi, P->alpha_lo};
   const dd malpha = dd_neg(alpha);
   dd rz{0.f, 0.f}, rr{0.f, 0.f};
+  // two vertices per thread (half grid), unrolled: more independent loads in flight
+#pragma unroll 2
   for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
     dd3_st(x, i, dd3_axpy(alpha, dd3_ld(p, i), dd3_ld(x, i)));
     dd3 qi = dd3_ld(q, i);
@@ -762,7 +764,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
           ++timed;
         }
         ::bal::note_launch();
-        BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, gv, kDdThreads, st, A, ex, (const dd*)ep,
+        BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, (gv + 1) / 2, kDdThreads, st, A, ex, (const dd*)ep,
                             (const dd*)eq, crow_of, (const dd*)eqc, er, ez, S.pcg, S.partials));
         ::bal::note_launch();
       }
