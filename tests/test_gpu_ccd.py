@@ -11,7 +11,7 @@ from oracle import bal as obal  # noqa: E402
 from oracle import ccd, contact, system  # noqa: E402
 from paper_2407_00046_b300 import bal  # noqa: E402
 
-from gpu_common import close_cubes  # noqa: E402
+from gpu_common import close_cubes, compare_trajectory  # noqa: E402
 
 DEV = "cuda"
 
@@ -78,12 +78,4 @@ def test_time_step_with_ccd_matches_oracle():
     S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12, pcg_max_iter=20000,
                                          step_mode=bal.STEP_CCD))
     m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    for _ in range(2):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8, step_mode="ccd"))
-        assert info["converged"] == 1
-        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
-        keys, d = obal.active_pairs(m, x.cpu().numpy().reshape(-1, 3))
-        assert len(d) == 0 or np.min(d) > 0.0
+    compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8, step_mode="ccd"), T)

@@ -13,7 +13,7 @@ from oracle import bal as obal  # noqa: E402
 from oracle import system  # noqa: E402
 from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 
-from gpu_common import close_cubes, oracle_state  # noqa: E402
+from gpu_common import close_cubes, compare_trajectory, oracle_state  # noqa: E402
 
 DEV = "cuda"
 
@@ -238,10 +238,4 @@ def test_df64_trajectory_matches_oracle():
     S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12, pcg_max_iter=20000,
                                          precision=bal.PREC_DF64))
     m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    for _ in range(2):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8))
-        assert info["converged"] == 1
-        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+    compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8), T)

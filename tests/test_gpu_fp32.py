@@ -19,7 +19,7 @@ from oracle import bal as obal  # noqa: E402
 from oracle import system  # noqa: E402
 from paper_2407_00046_b300 import bal  # noqa: E402
 
-from gpu_common import close_cubes, gpu_hessian, oracle_state  # noqa: E402
+from gpu_common import close_cubes, compare_trajectory, gpu_hessian, oracle_state  # noqa: E402
 
 DEV = "cuda"
 HESS_TOL_F32 = 5e-5
@@ -59,13 +59,7 @@ def test_fp32_time_step_matches_oracle():
     S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-10, precision=bal.PREC_FP32,
                                          mixed_max_refine=40))
     m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    for _ in range(2):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8))
-        assert info["converged"] == 1 and io["converged"]
-        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+    compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8), T)
 
 
 def test_fp32_solve_reports_its_precision():

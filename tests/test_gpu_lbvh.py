@@ -12,7 +12,7 @@ from oracle import bal as obal  # noqa: E402
 from oracle import contact, system  # noqa: E402
 from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 
-from gpu_common import close_cubes  # noqa: E402
+from gpu_common import close_cubes, compare_trajectory  # noqa: E402
 
 DEV = "cuda"
 
@@ -77,11 +77,4 @@ def test_time_step_with_lbvh_matches_oracle(mode):
                                          step_mode=bal.STEP_CCD if mode == "ccd" else bal.STEP_CA,
                                          broad_phase=bal.BROAD_LBVH))
     m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    for _ in range(2):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8, step_mode=mode,
-                                                           broad_phase="lbvh"))
-        assert info["converged"] == 1
-        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+    compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8, step_mode=mode, broad_phase="lbvh"), T)

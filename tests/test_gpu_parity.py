@@ -10,7 +10,7 @@ from oracle import bal as obal  # noqa: E402
 from oracle import system  # noqa: E402
 from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 
-from gpu_common import close_cubes, gpu_hessian, oracle_state  # noqa: E402
+from gpu_common import close_cubes, compare_trajectory, gpu_hessian, oracle_state  # noqa: E402
 
 DEV = "cuda"
 HESS_TOL = 1e-10      # |H_gpu - H_oracle|_max / |H_oracle|_max
@@ -135,24 +135,11 @@ def test_free_flight_is_exact():
     assert float((x - y).abs().max()) < 1e-13
 
 
-def _trajectory(sc, steps, newton_tol=1e-8):
-    S = bal.Scene(sc, bal.default_params(newton_tol=newton_tol, pcg_tol=1e-12, pcg_max_iter=20000))
-    m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    out = []
-    for _ in range(steps):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=newton_tol))
-        out.append((np.abs(x.cpu().numpy() - xo).max(), info, io))
-    return out
-
-
 def test_time_step_trajectory_small():
     sc = close_cubes(n=2, gap=5e-4)
-    for dx, info, io in _trajectory(sc, 3):
-        assert info["converged"] == 1 and io["converged"]
-        assert dx < 1e-8, (dx, info, io["iters"])
+    S = bal.Scene(sc, bal.default_params(newton_tol=1e-8, pcg_tol=1e-12, pcg_max_iter=20000))
+    m = system.make_model(sc)
+    assert compare_trajectory(S, m, sc, 3, obal.Params(newton_tol=1e-8), T) >= 1
 
 
 def test_newton_step_counts_match_oracle():
@@ -195,13 +182,7 @@ def test_mixed_precision_trajectory_matches_oracle():
                                          precision=bal.PREC_MIXED, mixed_inner_tol=1e-4,
                                          mixed_max_refine=40))
     m = system.make_model(sc)
-    x, v = T(sc.X), T(sc.V0)
-    xo, vo = sc.X.copy(), sc.V0.copy()
-    for _ in range(2):
-        info = S.time_step(x, v)
-        xo, vo, io = obal.time_step(m, xo, vo, obal.Params(newton_tol=1e-8))
-        assert info["converged"] == 1
-        assert np.abs(x.cpu().numpy() - xo).max() < 1e-8
+    compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8), T)
 
 
 def test_warm_start_solves_the_grouped_system(contact_case):
