@@ -300,10 +300,9 @@ __device__ dd contact_rows(const DDContact& Cr, const dd* __restrict__ p, dd* __
   return pq;
 }
 
-// q = (D + L + L^T) p over the slices (CTAs [0, n_row_ctas)) and the contact
-// part per contact row into qc (the CTAs after them; placing them first
-// measured 2% slower); partial sums of p . Hp; the last CTA to finish sets
-// alpha.
+// q = (D + L + L^T) p over the slices (n_row_ctas CTAs) and the contact part
+// per contact row into qc (the remaining CTAs, interleaved with them);
+// partial sums of p . Hp; the last CTA to finish sets alpha.
 __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, DDContact Cr, int n_row_ctas,
                                                         const dd* __restrict__ p, dd* __restrict__ q,
                                                         dd* __restrict__ qc, PcgScalars* P,
@@ -312,10 +311,18 @@ __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, DDContact Cr, i
   if (P->done) return;
   const int lane = threadIdx.x & 31;
   dd pq{0.f, 0.f};
-  if ((int)blockIdx.x >= n_row_ctas) {
-    pq = contact_rows<kContactLanes>(Cr, p, qc, blockIdx.x - n_row_ctas, gridDim.x - n_row_ctas);
+  // contact CTA j sits at grid position j K + K - 1 (K = grid / contact CTAs),
+  // so the contact rows' longer serial chains start throughout the launch and
+  // overlap the slice CTAs instead of forming a tail; the other positions are
+  // the slice CTAs in order
+  const int nc = gridDim.x - n_row_ctas;
+  const int K = nc > 0 ? (int)gridDim.x / nc : 1;
+  const int bj = blockIdx.x / K, br = blockIdx.x % K;
+  if (nc > 0 && br == K - 1 && bj < nc) {
+    pq = contact_rows<kContactLanes>(Cr, p, qc, bj, nc);
   } else {
-    for (int s = blockIdx.x * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += n_row_ctas * kDdWarps) {
+    const int bs = blockIdx.x - (nc > 0 ? min(nc, (int)(blockIdx.x + 1) / K) : 0);
+    for (int s = bs * kDdWarps + (threadIdx.x >> 5); s < A.ns; s += n_row_ctas * kDdWarps) {
       const int slot = 32 * s + lane;
       const int i = A.srow[slot];
       const bool own = i >= 0;
@@ -363,7 +370,8 @@ __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, c
   const dd alpha{P->alpha_hi, P->alpha_lo};
   const dd malpha = dd_neg(alpha);
   dd rz{0.f, 0.f}, rr{0.f, 0.f};
-  // two vertices per thread (half grid), unrolled: more independent loads in flight
+  // unrolled over two vertices per thread (on large meshes the grid is halved):
+  // more independent loads in flight
 #pragma unroll 2
   for (int i = blockIdx.x * NT + threadIdx.x; i < A.nv; i += gridDim.x * NT) {
     dd3_st(x, i, dd3_axpy(alpha, dd3_ld(p, i), dd3_ld(x, i)));
@@ -719,6 +727,9 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
   dd *ex = V, *er = V + n3, *ez = V + 2 * n3, *ep = V + 3 * n3, *eq = V + 4 * n3;
   const int gs = std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
   const int gv = std::min((nv + kDdThreads - 1) / kDdThreads, kMaxPartials / 2);   // one vertex per thread
+  // the update kernel takes two vertices per thread when that still leaves
+  // at least 4 CTAs per SM
+  const int gu = (gv + 1) / 2 >= 4 * kNumSM ? (gv + 1) / 2 : gv;
   // contact CTAs appended to the SpMV grid (none without contact)
   const int gc = Cr.n > 0 ? std::max(1, std::min((int)(((int64_t)Cr.n * kContactLanes + kDdThreads - 1) /
                                                        kDdThreads), kMaxPartials / 2))
@@ -764,7 +775,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
           ++timed;
         }
         ::bal::note_launch();
-        BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, (gv + 1) / 2, kDdThreads, st, A, ex, (const dd*)ep,
+        BAL_CUDA(launch_pdl(k_dd_update<kDdThreads>, gu, kDdThreads, st, A, ex, (const dd*)ep,
                             (const dd*)eq, crow_of, (const dd*)eqc, er, ez, S.pcg, S.partials));
         ::bal::note_launch();
       }
