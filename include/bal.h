@@ -233,6 +233,11 @@ BAL_API const char* bal_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far
  * (its own kernels; library sort / scan kernels are not counted). */
 BAL_API uint64_t bal_launch_count(void);
+/* sizeof of this build's ABI structs, for bindings to check their mirrors
+ * (no paper counterpart): which = 0 bal_params, 1 bal_scene_desc,
+ * 2 bal_bsr_view, 3 bal_al_state, 4 bal_solve_info, 5 bal_newton_info,
+ * 6 bal_step_info; 0 for any other value. Host-only, needs no GPU. */
+BAL_API uint64_t bal_struct_size(int32_t which);
 BAL_API void bal_default_params(bal_params* out);
 
 /* Copies the topology, precomputes D_m^{-1}, rest volumes, Lame parameters and

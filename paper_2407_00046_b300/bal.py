@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
     sigs = {
         "bal_last_error": ([], C.c_char_p),
         "bal_launch_count": ([], C.c_uint64),
+        "bal_struct_size": ([C.c_int32], C.c_uint64),
         "bal_default_params": ([C.POINTER(Params)], None),
         "bal_create_scene": ([C.POINTER(SceneDesc), C.POINTER(Params), C.POINTER(P)], C.c_int),
         "bal_destroy_scene": ([P], C.c_int),

@@ -544,6 +544,19 @@ const char* bal_last_error(void) { return g_err; }
 
 uint64_t bal_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+uint64_t bal_struct_size(int32_t which) {
+  switch (which) {
+    case 0: return sizeof(bal_params);
+    case 1: return sizeof(bal_scene_desc);
+    case 2: return sizeof(bal_bsr_view);
+    case 3: return sizeof(bal_al_state);
+    case 4: return sizeof(bal_solve_info);
+    case 5: return sizeof(bal_newton_info);
+    case 6: return sizeof(bal_step_info);
+    default: return 0;
+  }
+}
+
 static bool params_ok(const bal_params* p) {
   return p && !(!(p->pcg_tol >= 0) || p->pcg_max_iter < 0 || p->newton_max_iter < 0 ||
       p->precision < BAL_PREC_FP64 || p->precision > BAL_PREC_FP32 ||

@@ -33,6 +33,15 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_binding_structs_match_the_library_layout(lib):
+    import ctypes as C
+    mirrors = [bal.Params, bal.SceneDesc, bal.BsrView, bal.ALState, bal.SolveInfo, bal.NewtonInfo,
+               bal.StepInfo]
+    for which, cls in enumerate(mirrors):
+        assert lib.bal_struct_size(which) == C.sizeof(cls), cls.__name__
+    assert lib.bal_struct_size(99) == 0
+
+
 def test_default_params_follow_the_paper(lib):
     p = bal.default_params()
     assert p.newton_tol == 1e-4 and p.pcg_tol == 1e-4 and p.pcg_stall_window == 100
