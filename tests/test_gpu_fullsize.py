@@ -95,3 +95,40 @@ def test_sampled_rows_at_full_size(name):
     sol = torch.zeros_like(u1)
     info = S.pcg_solve(-g, sol, 1e-6, 1000)
     assert info["iters"] > 0 and np.isfinite(info["rel_residual"])
+
+
+def test_df64_solve_at_full_size():
+    """The benchmark's solver in its launch configuration (double-float PCG,
+    sliced-ELL SpMV, 1.77M-tet net, first Newton system of a step, relative
+    tolerance 1e-6, stagnation window 5000): every sampled residual row,
+    b_v - sum_u H_vu x_u with the oracle's rows of H and of b = -grad, stays
+    below the tolerance times ||b||, as a 2-norm bound on the whole residual
+    requires of each of its rows. Allowance for the two assemblies' rounding:
+    100 FP64 ulps of each row's sum of |H_vu x_u| (stiff 1 GPa rows sum terms
+    ~1e6 times larger than ||b||)."""
+    sc = scenes.scene_by_name("chain_net_shells")
+    rng = np.random.default_rng(10)
+    S = bal.Scene(sc, bal.default_params(precision=bal.PREC_DF64, pcg_stall_window=5000,
+                                         pcg_max_iter=30000), pair_capacity=1 << 22)
+    mass = S.mass()
+    x = sc.X.copy()
+    S.step_begin(T(sc.X), T(sc.V0))
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    S.assemble_hessian(T(x), g)
+    sol = torch.zeros_like(g)
+    tol = 1e-6
+    info = S.pcg_solve(-g, sol, tol, 30000)
+    assert info["converged"] == 1 and info["precision_used"] == bal.PREC_DF64
+    free = np.flatnonzero(sc.pinned == 0)
+    verts = [int(v) for v in rng.choice(free, 24, replace=False)]
+    ro, go = _oracle_rows(sc, x, verts, mass)
+    y = sc.X + sc.h * sc.V0 + sc.h ** 2 * sc.gravity[None, :]
+    xs = sol.cpu().numpy().reshape(-1, 3)
+    bnorm = float(torch.linalg.norm(g))
+    for v in verts:
+        b_v = -(go[v] + mass[v] * (x[v] - y[v]) / sc.h ** 2)
+        terms = [B @ xs[u] for u, B in ro[v].items() if not sc.pinned[u]]
+        r_v = b_v - sum(terms)
+        scale = sum(np.abs(B) @ np.abs(xs[u]) for u, B in ro[v].items() if not sc.pinned[u])
+        bound = 1.01 * tol * bnorm + 100 * np.finfo(np.float64).eps * np.linalg.norm(scale)
+        assert np.linalg.norm(r_v) <= bound, (v, np.linalg.norm(r_v), bound)
