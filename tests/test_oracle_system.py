@@ -114,3 +114,33 @@ def test_slack_elimination_closed_form():
         s_bf = s_grid[np.argmin(mu * c + 0.5 * sigma * c ** 2)]
         s_cf = max(-mu / sigma - dh + d, 0.0)
         assert abs(s_bf - s_cf) <= 1e-7
+
+
+def test_lambda_is_the_mean_clamped_eigenvalue_of_every_stencil(close_cubes):
+    """Lambda (Sec. 4.2.2) from eigenvalues rather than traces: every element,
+    contact pair and friction stencil adds the mean of the eigenvalues of its
+    projected Hessian to each of its 12 DOFs, on top of m / h^2."""
+    from oracle import elastic, friction
+    sc, m, x = close_cubes
+    rng = np.random.default_rng(31)
+    xd = x + 1e-4 * rng.normal(size=x.shape) * (sc.pinned == 0)[:, None]
+    y = system.inertia_target(m, sc.X, sc.V0)
+    keys, _ = bal.active_pairs(m, xd)
+    assert keys
+    ps = _pairset(m, xd, keys, {})
+    fs = bal.friction_set(m, xd, x, ps, 5.0, bal.Params(friction=0.4))
+    _, lam = system.hessian(m, xd, y, ps, 5.0, with_lambda=True, fric=fs)
+    ref = np.repeat(m.mass / m.h ** 2, 3)
+
+    def add(nodes, H):
+        mean = np.linalg.eigvalsh(H).mean(axis=1)
+        for k in range(4):
+            for a in range(3):
+                np.add.at(ref, 3 * nodes[:, k] + a, mean)
+
+    _, _, He = elastic.element_terms(xd, sc.tets, m.Dm_inv, m.vol, m.mu, m.lam, project=True)
+    add(sc.tets.astype(np.int64), He)
+    _, _, Hc, nodes, _ = contact.contact_terms(xd, ps.keys, sc, ps.inA, ps.inAp, ps.mu, ps.s, 5.0, m.dhat)
+    add(nodes, Hc)
+    add(fs.nodes, friction.terms(fs, xd)[2])
+    assert np.abs(lam - ref).max() <= 1e-12 * np.abs(ref).max()
