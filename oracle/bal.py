@@ -98,6 +98,42 @@ def initial_sigma(model, x, y, A_keys):
     return max(-float(np.sum(gb * gE)) / nb2, floor)
 
 
+def sigma_update(sigma, sigma0, dmin, prm: Params, dhat):
+    """Alg. 1 line 16: when min d < 1e-2 dhat, sigma <- max(1.2 sigma, 100 sigma0)
+    (the printed rule, `sigma_literal_max`) or min(1.2 sigma, 100 sigma0) (the
+    capped reading); otherwise sigma is kept."""
+    if not dmin < prm.ap_ratio * dhat:
+        return sigma
+    if prm.sigma_literal_max:
+        return max(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
+    return min(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
+
+
+def augmentation_set(Ap, A_keys, A_d, dmin, dmin_prev, prm: Params, dhat):
+    """Alg. 1 lines 3-6: A' = {} when min d > 1e-2 dhat; rebuilt from the pairs
+    of A with d < 1e-2 dhat when min d fell below the previous iterate's or A'
+    is empty (mu kept for pairs that stay, 0 for new ones); kept otherwise.
+    Ap maps pair key -> mu; returns the new map."""
+    thr = prm.ap_ratio * dhat
+    if dmin > thr:
+        return {}
+    if dmin < dmin_prev or not Ap:
+        return {k: Ap.get(k, 0.0) for k, dd in zip(A_keys, A_d) if dd < thr}
+    return dict(Ap)
+
+
+def dual_update(Ap, d_ap, sigma, dhat):
+    """Alg. 1 lines 12-15 for every pair of A' (keys in sorted order, distances
+    d_ap at the new iterate): s_i re-evaluated there (Sec. 3.2.2), then
+    mu_i += sigma b(d_i, dhat + s_i)."""
+    out = {}
+    for k, dd in zip(sorted(Ap), d_ap):
+        mu = Ap[k]
+        s = max(-mu / sigma - dhat + dd, 0.0)
+        out[k] = mu + sigma * float(barrier.b(np.array([dd]), dhat + s)[0])
+    return out
+
+
 def make_pairset(model, x, A_keys, Ap, sigma):
     keys = sorted(set(A_keys) | set(Ap))
     if not keys:
@@ -168,10 +204,10 @@ def friction_set(model, x, x_t, ps: PairSet, sigma, prm: Params):
     """Friction data of the pairs of ps lagged at x (None when chi = 0)."""
     if prm.friction <= 0.0 or not ps.keys:
         return None
-    d, regions, nodes = contact.pair_distances(x, ps.keys, model.scene)
-    _, e1, _ = contact.phi_derivs(d, ps.inA, ps.inAp, ps.mu, ps.s, sigma, model.dhat)
+    lam, regions, nodes = contact.normal_forces(x, ps.keys, model.scene, ps.inA, ps.inAp, ps.mu,
+                                                ps.s, sigma, model.dhat)
     eps_v = prm.eps_v if prm.eps_v > 0.0 else model.dhat
-    return friction.lag(x, x_t, nodes, regions, -e1, prm.friction, eps_v * model.h)
+    return friction.lag(x, x_t, nodes, regions, lam, prm.friction, eps_v * model.h)
 
 
 def line_search(model, x, y, p, ps: PairSet, sigma, prm: Params, fric=None):
@@ -262,26 +298,14 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
         if l > 0 and frozen is None and not plain:
             # dual update of the previous iteration, evaluated at x^[l]
             if Ap:
-                keys = sorted(Ap)
-                d_ap, _, _ = contact.pair_distances(x, keys, model.scene)
-                for k, dd in zip(keys, d_ap):
-                    mu = Ap[k]
-                    s = max(-mu / sigma - dh + dd, 0.0)
-                    Ap[k] = mu + sigma * float(barrier.b(np.array([dd]), dh + s)[0])
-            if dmin < prm.ap_ratio * dh:
-                if prm.sigma_literal_max:
-                    sigma = max(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
-                else:
-                    sigma = min(prm.sigma_growth * sigma, prm.sigma_cap * sigma0)
+                d_ap, _, _ = contact.pair_distances(x, sorted(Ap), model.scene)
+                Ap = dual_update(Ap, d_ap, sigma, dh)
+            sigma = sigma_update(sigma, sigma0, dmin, prm, dh)
         # augmentation set rule (Alg. 1 lines 3-6)
         if plain:
             Ap = {}
-        elif frozen is not None:
-            pass
-        elif dmin > prm.ap_ratio * dh:
-            Ap = {}
-        elif dmin < dmin_prev or not Ap:
-            Ap = {k: Ap.get(k, 0.0) for k, dd in zip(A_keys, A_d) if dd < prm.ap_ratio * dh}
+        elif frozen is None:
+            Ap = augmentation_set(Ap, A_keys, A_d, dmin, dmin_prev, prm, dh)
         dmin_prev = dmin
         ps = make_pairset(model, x, A_keys, Ap, sigma)
         fs = friction_set(model, x, x_t, ps, sigma, prm)

@@ -16,9 +16,26 @@ Per pair i the energy of Eq. (aug-lag) is a function of d_i only:
 so grad = phi' grad d and Hessian = phi'' grad d grad d^T + phi' Hess d; the
 12x12 stencil Hessian is then projected to the nearest PSD matrix
 (Sec. 4.2.2). s_i (Sec. 3.2.2) is held fixed inside an iteration.
+
+Edge-edge pairs are mollified (reading: the paper takes its contact potential
+from IPC and is silent on parallel edges; IPC, Li et al. 2020, Sec. 4.3, scales
+every edge-edge term by a mollifier because the segment-segment distance is
+not C^1 where the edges become parallel):
+
+    phi_EE(x) = m(c) phi(d),  c = |u x v|^2  (u, v the two edge vectors),
+    m(c) = (2 - c/eps_x) c/eps_x for c < eps_x, else 1,
+    eps_x = 1e-3 |u_rest|^2 |v_rest|^2,
+
+so grad = m phi' grad d + phi grad m and
+Hessian = m (phi'' grad d grad d^T + phi' Hess d)
+          + phi' (grad d grad m^T + grad m grad d^T) + phi Hess m,
+projected as one 12x12 block. Derivatives of m are taken by automatic
+differentiation of m(c(x)).
 """
 import numpy as np
+import torch
 from scipy.spatial import cKDTree
+from torch.func import grad, hessian, vmap
 
 from . import barrier, distance
 from .elastic import project_psd
@@ -104,6 +121,73 @@ def phi_derivs(d, inA, inAp, mu, s, sigma, dhat):
     return e, e1, e2
 
 
+MOLLIFIER_EPS = 1e-3    # eps_x = 1e-3 |u_rest|^2 |v_rest|^2 (IPC)
+MOLLIFY_EE = True
+
+
+def ee_eps(pairs, scene):
+    """eps_x of every pair from the rest positions (0 for point-triangle pairs
+    and when mollification is off)."""
+    out = np.zeros(len(pairs))
+    if not MOLLIFY_EE or not len(pairs):
+        return out
+    P = np.asarray(pairs, dtype=np.int64).reshape(-1, 3)
+    ee = P[:, 0] == 1
+    if ee.any():
+        Xr = np.asarray(scene.X, dtype=np.float64)
+        ea, eb = scene.edges[P[ee, 1]], scene.edges[P[ee, 2]]
+        u = Xr[ea[:, 1]] - Xr[ea[:, 0]]
+        v = Xr[eb[:, 1]] - Xr[eb[:, 0]]
+        out[ee] = MOLLIFIER_EPS * np.sum(u * u, axis=1) * np.sum(v * v, axis=1)
+    return out
+
+
+def _m_of_x(x, eps):
+    X = x.reshape(4, 3)
+    n = torch.linalg.cross(X[1] - X[0], X[3] - X[2])
+    r = (n @ n) / eps
+    return torch.where(r < 1.0, (2.0 - r) * r, torch.ones_like(r))
+
+
+def mollifier(X4, eps, derivs=True):
+    """m [n] (and grad m [n,12], Hessian of m [n,12,12]) of the edge-edge
+    mollifier at stencil positions X4 [n,4,3]; rows with eps = 0 get m = 1."""
+    n = X4.shape[0]
+    m = np.ones(n)
+    gm = np.zeros((n, 12))
+    Hm = np.zeros((n, 12, 12))
+    idx = np.flatnonzero(np.asarray(eps) > 0)
+    if idx.size:
+        xs = torch.from_numpy(np.ascontiguousarray(X4[idx].reshape(idx.size, 12))).double()
+        es = torch.from_numpy(np.asarray(eps, dtype=np.float64)[idx])
+        m[idx] = vmap(_m_of_x)(xs, es).numpy()
+        if derivs:
+            gm[idx] = vmap(grad(_m_of_x))(xs, es).numpy()
+            Hm[idx] = vmap(hessian(_m_of_x))(xs, es).numpy()
+    if derivs:
+        return m, gm, Hm
+    return m
+
+
+def pair_energies(x, pairs, scene, inA, inAp, mu, s, sigma, dhat):
+    """Per-pair energy phi_i at x (edge-edge pairs mollified), for the
+    objective and the line search."""
+    if not len(pairs):
+        return np.zeros(0)
+    d, _, nodes = pair_distances(x, pairs, scene)
+    e, _, _ = phi_derivs(d, inA, inAp, mu, s, sigma, dhat)
+    return e * mollifier(x[nodes], ee_eps(pairs, scene), derivs=False)
+
+
+def normal_forces(x, pairs, scene, inA, inAp, mu, s, sigma, dhat):
+    """Normal force magnitude -m phi'(d) of every pair at x (the lagged lambda
+    of friction), with the distances' regions and the stencil nodes."""
+    d, regions, nodes = pair_distances(x, pairs, scene)
+    _, e1, _ = phi_derivs(d, inA, inAp, mu, s, sigma, dhat)
+    m = mollifier(x[nodes], ee_eps(pairs, scene), derivs=False)
+    return -m * e1, regions, nodes
+
+
 def contact_terms(x, pairs, scene, inA, inAp, mu, s, sigma, dhat, project=True):
     """Per-pair energy [n], gradient [n,12], Hessian [n,12,12] (projected),
     stencil nodes [n,4] and distances [n]."""
@@ -119,6 +203,12 @@ def contact_terms(x, pairs, scene, inA, inAp, mu, s, sigma, dhat, project=True):
     e, e1, e2 = phi_derivs(d, inA, inAp, mu, s, sigma, dhat)
     g = e1[:, None] * gd
     H = e2[:, None, None] * gd[:, :, None] * gd[:, None, :] + e1[:, None, None] * Hd
+    m, gm, Hm = mollifier(X4, ee_eps(pairs, scene))
+    H = (m[:, None, None] * H + e1[:, None, None] * (gd[:, :, None] * gm[:, None, :]
+                                                     + gm[:, :, None] * gd[:, None, :])
+         + e[:, None, None] * Hm)
+    g = m[:, None] * g + e[:, None] * gm
+    e = m * e
     if project:
         H = project_psd(H)
     return e, g, H, nodes, d

@@ -85,8 +85,8 @@ def energy_parts(model, x, y, pairs: PairSet, sigma, fric=None):
     el = float(np.sum(model.vol * elastic.psi(F, model.mu, model.lam)))
     con = 0.0
     if pairs.keys:
-        d, _, _ = contact.pair_distances(x, pairs.keys, sc)
-        e, _, _ = contact.phi_derivs(d, pairs.inA, pairs.inAp, pairs.mu, pairs.s, sigma, model.dhat)
+        e = contact.pair_energies(x, pairs.keys, sc, pairs.inA, pairs.inAp, pairs.mu, pairs.s,
+                                  sigma, model.dhat)
         con = float(np.sum(e))
     con += friction.energy(fric, x)
     return float(inertia), el, con

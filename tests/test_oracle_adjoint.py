@@ -51,7 +51,6 @@ def test_adjoint_matches_central_fd_through_contact():
     J, gx = _loss(model, xT, body, target)
     _, dv0, dE = adjoint.backward(model, ck, gx, np.zeros_like(gx))
     frozen = [(c[3], c[4]) for c in ck]     # perturbed runs keep each step's AL state
-    assert any(len(f[1]) > 0 or True for f in frozen)
     rng = np.random.default_rng(0)
     # directional derivative in E: J(E (1 + eps w))
     w = rng.choice([-1.0, 1.0], size=sc.n_tets)
