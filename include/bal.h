@@ -74,8 +74,9 @@ typedef struct {
   int32_t newton_max_iter;
   double ap_ratio;            /* A' threshold factor (1e-2) */
   double sigma_growth;        /* 1.2 */
-  double sigma_cap;           /* 100 (times sigma0) */
-  int32_t sigma_literal_max;  /* 1 = printed max(1.2 s, 100 s0) rule */
+  double sigma_cap;           /* 100: multiple of sigma0 in the sigma schedule */
+  int32_t sigma_literal_max;  /* 1 (default) = the printed max(1.2 s, 100 s0) rule of Alg. 1;
+                                 0 = the capped reading min(1.2 s, 100 s0) */
   double step_bound;          /* 0.9: CA keeps (1 - step_bound) of each gap; CCD: margin on the TOI */
   double ls_min_alpha;        /* 1e-9 (App. B) */
   double ls_slack;            /* relative energy slack for rounding noise (1e-12) */
@@ -99,6 +100,12 @@ typedef struct {
                                  closest-point weights lagged at each Newton iterate */
   double friction_eps_v;      /* mollifier threshold eps_v (m/s; 0 = dhat, Table 1 caption);
                                  the static zone is |tangent slip| < eps_v h */
+  int32_t spmv_window;        /* double-float SpMV layout: 0 = one thread per row gathering
+                                 every transposed block through its column-side list; W > 0
+                                 (a multiple of 32, at most 4096) = one CTA per window of W
+                                 consecutive rows, transposed blocks of rows in the same
+                                 window summed in shared memory (FP64), only the other
+                                 windows' through the column-side list */
 } bal_params;
 
 /* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain
@@ -257,6 +264,20 @@ BAL_API bal_status bal_set_params(bal_scene* scene, const bal_params* params);
  * Not in the paper: measurement support. */
 BAL_API bal_status bal_kernel_timing(bal_scene* scene, int32_t enable, double* total_ms,
                                      int64_t* launches);
+/* FP64 FMA throughput of the current device in TFLOP/s (2 flop per FMA), from
+ * one timed launch of `iters` FMA rounds on 8 independent chains per thread
+ * over 8 CTAs of 256 threads per SM: the ALU ceiling of the FP64 kernels.
+ * Allocates and frees a small scratch buffer on `stream`. Not in the paper:
+ * measurement support. */
+BAL_API bal_status bal_fp64_fma_rate(int32_t iters, double* tflops, void* stream);
+/* Assembly timing under the same switch: per assemble call, CUDA events on
+ * its stream around the element Hessian kernel and around the whole assembly
+ * (element stencils, contact stencils, duplicate-block merge, D^-1). Returns
+ * the sums since the previous call (either pointer may be NULL) and the
+ * number of timed assemblies, and resets them. Not in the paper:
+ * measurement support. */
+BAL_API bal_status bal_assembly_timing(bal_scene* scene, double* elastic_ms, double* total_ms,
+                                       int64_t* assemblies);
 
 BAL_API bal_status bal_get_params(const bal_scene* scene, bal_params* out);
 /* Host copies of the static pattern: row_ptr [n_verts+1], col [nnz_L]; either
@@ -332,6 +353,9 @@ BAL_API bal_status bal_step_bound(bal_scene* scene, const double* x, const doubl
  * bound, backtracking line search (Sec. 5.2 memory cap). */
 BAL_API bal_status bal_newton_step(bal_scene* scene, double* x_inout, bal_newton_info* info,
                            void* stream);
+/* Ends the current time step at x (device): v_out = (x - x_t) / h (Sec. 3.1),
+ * x_t being the state passed to bal_step_begin. v_out is device [n_verts*3]. */
+BAL_API bal_status bal_step_end(bal_scene* scene, const double* x, double* v_out, void* stream);
 /* Full time step: bal_step_begin + Alg. 1 loop + v = (x - x_t)/h (Sec. 3.1). */
 BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_inout,
                          bal_step_info* info, void* stream);
@@ -339,8 +363,10 @@ BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_in
 /* ---- allocation-free solve (no counterpart in the paper) -------------------- */
 /* For callers that cannot allocate GPU memory while they run (a host
  * application that owns all device memory, or a loop that forbids allocation
- * after start-up): block-Jacobi PCG, same stopping rules as bal_pcg_solve
- * (stagnation window 100), on a caller-provided symmetric block matrix
+ * after start-up): block-Jacobi PCG with the stopping rules of bal_pcg_solve
+ * under the default parameters (||r|| <= rel_tol ||r_0||, no new minimum of
+ * the preconditioned residual sqrt(r^T z) in 100 iterations, or max_iter), on
+ * a caller-provided symmetric block matrix
  * H = D + L + L^T in DEVICE memory -- D [n_verts][9] diagonal blocks, nnz lower
  * blocks (rows[nnz], cols[nnz] with rows > cols, vals[nnz][9] row-major) --
  * solving H sol = rhs from the initial guess in sol (device, in/out). It calls
@@ -348,8 +374,11 @@ BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_in
  * of about 2.8 MB that every GPU loading the library keeps until exit, so
  * n_verts may not exceed BAL_NOALLOC_MAX_VERTS (larger sizes return
  * BAL_ERR_ARG). The first call on a device looks up that array's address and
- * should come before any stream capture. All calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * should come before any stream capture; the address is cached per device
+ * index for the life of the process, which assumes the device's primary
+ * context throughout (no cudaDeviceReset between calls). All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller. A non-finite residual or p^T H p <= 0 returns BAL_ERR_NAN. */
 #define BAL_NOALLOC_MAX_VERTS 16384
 BAL_API bal_status bal_pcg_solve_noalloc(int32_t n_verts, const double* D, int64_t nnz,
                                          const int32_t* rows, const int32_t* cols,

@@ -15,8 +15,10 @@ paper used here (each one is recorded in the design notes):
 * s_i = max(-mu_i/sigma - dhat + d_i, 0) is evaluated at the start of an
   iteration and held fixed inside it; the dual update re-evaluates it at the
   new iterate before mu_i += sigma b(d_i, dhat + s_i);
-* sigma update: sigma <- min(1.2 sigma, 100 sigma0) (the printed max(...) is
-  read as a cap; the literal form is available as `sigma_literal_max`);
+* sigma update: sigma <- max(1.2 sigma, 100 sigma0) whenever min d < 1e-2 dhat,
+  as printed (Alg. 1): a jump to 100 sigma0, then 1.2x growth per iteration
+  until the closest pair is back above 1e-2 dhat; the capped reading
+  min(1.2 sigma, 100 sigma0) is `sigma_literal_max = False`;
 * sigma0 = -(sum grad b)^T grad E / ||sum grad b||^2 over A (the printed
   denominator is not squared, which is not dimensionally consistent), floored
   at mbar / (h^2 b''(dhat/2, dhat)); evaluated at x_0, or, when A(x_0) is empty,
@@ -55,7 +57,7 @@ class Params:
     ap_ratio: float = 1e-2          # A' threshold 1e-2 dhat (Alg. 1)
     sigma_growth: float = 1.2
     sigma_cap: float = 100.0
-    sigma_literal_max: bool = False
+    sigma_literal_max: bool = True
     step_bound: float = 0.9
     ls_min_alpha: float = 1e-9      # App. B
     ls_slack: float = 1e-12
@@ -68,6 +70,7 @@ class Params:
                                     # (boxes swept along the step within dhat)
     friction: float = 0.0           # chi (Sec. 4.1); 0 = frictionless
     eps_v: float = 0.0              # mollifier threshold (m/s); 0 = dhat (Table 1 caption)
+    elastic_projection: str = "F"   # "F": 9x9 dP/dF (both paths); "stencil": 12x12 element block
 
 
 def sigma_floor(model):
@@ -318,7 +321,7 @@ def time_step(model, x_t, v_t, prm: Params = Params(), log=None, frozen=None):
         if en <= prm.newton_abs_tol or (l > 0 and en <= prm.newton_tol * e0):
             info["converged"] = True
             break
-        H = hessian(model, x, y, ps, sigma, fric=fs)
+        H = hessian(model, x, y, ps, sigma, fric=fs, elastic_projection=prm.elastic_projection)
         p = solve(H, -e.ravel()).reshape(-1, 3)
         alpha, xn, lsi = line_search(model, x, y, p, ps, sigma, prm, fs)
         rec["alpha"] = alpha

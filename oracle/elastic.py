@@ -123,15 +123,20 @@ def project_psd(H):
 
 
 def element_terms(x, tets, Dm_inv, vol, mu, lam, project=True):
-    """Per-tet energy W_e [N_t], gradient [N_t,12] and Hessian [N_t,12,12]
-    (PSD-projected in F-space when project=True)."""
+    """Per-tet energy W_e [N_t], gradient [N_t,12] and Hessian [N_t,12,12].
+    project: False (exact Hessian), True or "F" (PSD projection of the 9x9
+    dP/dF, the reading used by both paths), or "stencil" (the nearest PSD
+    matrix to the 12x12 element block V_e G^T (dP/dF) G itself, the other
+    reading of Sec. 4.2.2, kept to measure the difference)."""
     F = deformation_gradient(x, tets, Dm_inv)
     W = vol * psi(F, mu, lam)
     P = first_piola(F, mu, lam)
     G = grad_map(Dm_inv)
     g = vol[:, None] * np.einsum("nab,na->nb", G, P.reshape(-1, 9))
     K = dPdF(F, mu, lam)
-    if project:
+    if project is True or project == "F":
         K = project_psd(K)
     H = vol[:, None, None] * np.einsum("nai,nab,nbj->nij", G, K, G)
+    if project == "stencil":
+        H = project_psd(H)
     return W, g, H

@@ -136,15 +136,17 @@ def _coo_blocks(nodes, H, n_dof):
     return rows, cols, H.ravel()
 
 
-def hessian(model, x, y, pairs: PairSet, sigma, project=True, with_lambda=False, fric=None):
+def hessian(model, x, y, pairs: PairSet, sigma, project=True, with_lambda=False, fric=None,
+            elastic_projection="F"):
     """Assembled PSD-projected Hessian of L_sigma as scipy CSR [3N_v, 3N_v],
     pinned rows / columns eliminated with diagonal m/h^2. Friction stencils
     (PSD by construction, not projected) add their Hessians and their trace
-    means to Lambda."""
+    means to Lambda. elastic_projection: "F" (9x9 dP/dF, both paths) or
+    "stencil" (12x12 element block) when project is set."""
     sc = model.scene
     nd = 3 * model.n
     _, _, He = elastic.element_terms(x, sc.tets, model.Dm_inv, model.vol, model.mu,
-                                     model.lam, project=project)
+                                     model.lam, project=elastic_projection if project else False)
     r1, c1, v1 = _coo_blocks(sc.tets.astype(np.int64), He, nd)
     rows, cols, vals = [r1], [c1], [v1]
     lam = np.repeat(model.mass / model.h ** 2, 3)

@@ -46,7 +46,8 @@ class Params(C.Structure):
                 ("mixed_max_refine", C.c_int32), ("ca_max_iter", C.c_int32),
                 ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32),
                 ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32),
-                ("friction", C.c_double), ("friction_eps_v", C.c_double)]
+                ("friction", C.c_double), ("friction_eps_v", C.c_double),
+                ("spmv_window", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -127,11 +128,15 @@ def load(path: str = LIB_PATH):
         "bal_set_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_get_params": ([P, C.POINTER(Params)], C.c_int),
         "bal_kernel_timing": ([P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+        "bal_fp64_fma_rate": ([C.c_int32, C.POINTER(C.c_double), P], C.c_int),
+        "bal_assembly_timing": ([P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+                                C.c_int),
         "bal_step_bound": ([P, P, P, P, C.c_int64, C.c_int32, C.POINTER(C.c_double), P], C.c_int),
         "bal_find_candidates": ([P, P, P, C.c_double, P, C.c_int64, C.POINTER(C.c_int64), P], C.c_int),
         "bal_static_pattern": ([P, C.POINTER(C.c_int64), P, P], C.c_int),
         "bal_get_mass": ([P, P], C.c_int),
         "bal_step_begin": ([P, P, P, P], C.c_int),
+        "bal_step_end": ([P, P, P, P], C.c_int),
         "bal_get_al_state": ([P, C.POINTER(ALState), C.c_int64], C.c_int),
         "bal_set_al_state": ([P, C.POINTER(ALState)], C.c_int),
         "bal_get_y": ([P, P, P], C.c_int),
@@ -159,6 +164,18 @@ def load(path: str = LIB_PATH):
 def _check(status):
     if status != OK:
         raise BalError(status, load().bal_last_error().decode())
+
+
+def fp64_fma_rate(iters: int = 20000, stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(load().bal_fp64_fma_rate(int(iters), C.byref(t), _stream(stream)))
+    return t.value
+
+
+def last_error() -> str:
+    """The library's message for the last failed call on this thread."""
+    return load().bal_last_error().decode()
 
 
 def launch_count() -> int:
@@ -253,6 +270,12 @@ class Scene:
         _check(load().bal_kernel_timing(self._h, int(bool(enable)), C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def assembly_timing(self):
+        """(element-kernel ms, whole-assembly ms, assemblies) since the last call."""
+        e, t, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(load().bal_assembly_timing(self._h, C.byref(e), C.byref(t), C.byref(n)))
+        return e.value, t.value, n.value
+
     def get_params(self) -> Params:
         p = Params()
         _check(load().bal_get_params(self._h, C.byref(p)))
@@ -278,6 +301,13 @@ class Scene:
         n = 3 * self.nv
         _check(load().bal_step_begin(self._h, _dev(x_t, torch.float64, n), _dev(v_t, torch.float64, n),
                                      _stream(stream)))
+
+    def step_end(self, x, v_out, stream=None):
+        """v_out = (x - x_t) / h for the step begun by step_begin (device)."""
+        import torch
+        n = 3 * self.nv
+        _check(load().bal_step_end(self._h, _dev(x, torch.float64, n), _dev(v_out, torch.float64, n),
+                                   _stream(stream)))
 
     def get_al_state(self):
         st = ALState()
@@ -379,12 +409,16 @@ class Scene:
                                      _stream(stream)))
         return a.value
 
-    def newton_step(self, x, stream=None):
+    def newton_step(self, x, stream=None, check=True):
         import torch
         info = NewtonInfo()
-        _check(load().bal_newton_step(self._h, _dev(x, torch.float64, 3 * self.nv), C.byref(info),
-                                      _stream(stream)))
-        return _as_dict(info)
+        s = load().bal_newton_step(self._h, _dev(x, torch.float64, 3 * self.nv), C.byref(info),
+                                   _stream(stream))
+        if check:
+            _check(s)
+        d = _as_dict(info)
+        d["status"] = s
+        return d
 
     def set_materials(self, E, nu=None):
         """Per-tet Young's modulus (and Poisson ratio) from host arrays."""

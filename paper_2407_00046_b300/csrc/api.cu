@@ -222,10 +222,21 @@ bal_status gradient(Scene& S, const double* x, double* g, cudaStream_t st) {
 
 // projected Hessian at x (eval list must be current); contact gradient into g if non-null
 bal_status assemble(Scene& S, const double* x, double* g, cudaStream_t st) {
+  if (S.ktime) BAL_CUDA(cudaEventRecord(S.kaev[2], st));
   BAL_TRY(launch_elastic_assemble(S, x, st));
   BAL_TRY(launch_contact_terms(S, x, g, true, st));
   BAL_TRY(contact_blocks_reduce(S, 6 * S.n_eval, st));
   BAL_TRY(launch_dinv(S, st));
+  if (S.ktime) {
+    BAL_CUDA(cudaEventRecord(S.kaev[3], st));
+    BAL_CUDA(cudaEventSynchronize(S.kaev[3]));
+    float e = 0.f, t = 0.f;
+    if (S.d.nt > 0) BAL_CUDA(cudaEventElapsedTime(&e, S.kaev[0], S.kaev[1]));
+    BAL_CUDA(cudaEventElapsedTime(&t, S.kaev[2], S.kaev[3]));
+    S.ka_elastic_ms += e;
+    S.ka_total_ms += t;
+    S.ka_n += 1;
+  }
   S.assembled = true;
   S.f32_valid = false;
   S.dd_valid = false;
@@ -566,7 +577,8 @@ static bool params_ok(const bal_params* p) {
       p->al_mode < BAL_AL_ALGORITHM1 || p->al_mode > BAL_AL_PLAIN ||
       p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_COND_B ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
-      !(p->friction >= 0) || !(p->friction_eps_v >= 0));
+      !(p->friction >= 0) || !(p->friction_eps_v >= 0) ||
+      p->spmv_window < 0 || p->spmv_window > 4096 || (p->spmv_window % 32) != 0);
 }
 
 void bal_default_params(bal_params* p) {
@@ -583,7 +595,7 @@ void bal_default_params(bal_params* p) {
   p->ap_ratio = 1e-2;
   p->sigma_growth = 1.2;
   p->sigma_cap = 100.0;
-  p->sigma_literal_max = 0;
+  p->sigma_literal_max = 1;
   p->step_bound = 0.9;
   p->ls_min_alpha = 1e-9;
   p->ls_slack = 1e-12;
@@ -602,6 +614,7 @@ void bal_default_params(bal_params* p) {
   p->pcg_tol_mode = BAL_PCG_TOL_FIXED;
   p->friction = 0.0;
   p->friction_eps_v = 0.0;
+  p->spmv_window = 0;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -760,11 +773,14 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   for (double& c : bcnt) c = 1.0 / c;
   S.nbody = (int32_t)bcnt.size();
   // mean surface edge length at rest (grid cell size)
+  // and the rest squared length of every surface edge (edge-edge mollifier)
   double el = 0.0;
+  std::vector<double> edge_l2(desc->n_edges);
   for (int e = 0; e < desc->n_edges; ++e) {
     const int a = desc->edges[2 * e], b = desc->edges[2 * e + 1];
     double s2 = 0;
     for (int i = 0; i < 3; ++i) s2 += (X[3 * a + i] - X[3 * b + i]) * (X[3 * a + i] - X[3 * b + i]);
+    edge_l2[e] = s2;
     el += std::sqrt(s2);
   }
   S.mean_edge = desc->n_edges ? el / desc->n_edges : 1e-3;
@@ -778,6 +794,7 @@ bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params
   TRYC(dupload(S, &S.d.tets, desc->tets, 4 * (size_t)nt));
   TRYC(dupload(S, &S.d.tris, desc->tris, 3 * (size_t)desc->n_tris));
   TRYC(dupload(S, &S.d.edges, desc->edges, 2 * (size_t)desc->n_edges));
+  TRYC(dupload(S, &S.d.edge_l2, (const double*)edge_l2.data(), edge_l2.size()));
   TRYC(dupload(S, &S.d.surf, desc->surf_verts, (size_t)desc->n_surf_verts));
   TRYC(dupload(S, &S.d.pinned, desc->pinned, (size_t)nv));
   TRYC(dupload(S, &S.d.Dm_inv, (const double*)Dmi.data(), Dmi.size()));
@@ -852,8 +869,10 @@ bal_status bal_destroy_scene(bal_scene* sc) {
   for (void* p : S.owned) cudaFree(p);
   for (cudaEvent_t& e : S.kev)
     if (e) cudaEventDestroy(e);
-  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_keys_alt, &S.emit_idx,
-                 &S.emit_idx_alt, &S.emit_vals, &S.seg_head, &S.seg_pos, &S.cub_tmp, &S.bp_cells,
+  for (cudaEvent_t& e : S.kaev)
+    if (e) cudaEventDestroy(e);
+  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_vals, &S.cm_cnt,
+                 &S.cm_off, &S.cm_bucket, &S.cm_sorted, &S.cm_ucnt, &S.cm_uoff, &S.scan_aux, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,
                  &S.ls_cand, &S.ls_cand_alt, &S.bstats, &S.ap_keys_d, &S.ap_mu_d, &S.ap_s_d,
@@ -886,9 +905,22 @@ bal_status bal_kernel_timing(bal_scene* sc, int32_t enable, double* total_ms, in
   if (launches) *launches = S.kt_n;
   S.kt_ms = 0;
   S.kt_n = 0;
-  if (enable && !S.kev[0])
+  if (enable && !S.kev[0]) {
     for (cudaEvent_t& e : S.kev) BAL_CUDA(cudaEventCreate(&e));
+    for (cudaEvent_t& e : S.kaev) BAL_CUDA(cudaEventCreate(&e));
+  }
   S.ktime = enable != 0;
+  return BAL_OK;
+}
+
+bal_status bal_assembly_timing(bal_scene* sc, double* elastic_ms, double* total_ms, int64_t* assemblies) {
+  BAL_TRY(check_scene(sc));
+  Scene& S = sc->S;
+  if (elastic_ms) *elastic_ms = S.ka_elastic_ms;
+  if (total_ms) *total_ms = S.ka_total_ms;
+  if (assemblies) *assemblies = S.ka_n;
+  S.ka_elastic_ms = S.ka_total_ms = 0;
+  S.ka_n = 0;
   return BAL_OK;
 }
 
@@ -1228,6 +1260,21 @@ bal_status bal_adjoint_step(bal_scene* sc, const double* x_t, const double* v_t,
   BAL_TRY(launch_dLdE(S, x_next, S.dir, dE, st));
   BAL_CUDA(cudaStreamSynchronize(st));
   if (info) *info = si;
+  return BAL_OK;
+}
+
+bal_status bal_step_end(bal_scene* sc, const double* x, double* v, void* stream) {
+  BAL_TRY(check_scene(sc));
+  if (!x || !v) {
+    set_error("bal_step_end: null x or v");
+    return BAL_ERR_ARG;
+  }
+  Scene& S = sc->S;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n3 = 3 * (int64_t)S.d.nv;
+  k_velocity<<<grid_for(n3), kThreads, 0, st>>>(n3, 1.0 / S.d.h, x, S.xt, v);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
   return BAL_OK;
 }
 

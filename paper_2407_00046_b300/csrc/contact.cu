@@ -196,6 +196,68 @@ __device__ inline double d2bar(double d, double c) {
   return -2.0 * log(d / c) - 4.0 * t / d + t * t / (d * d);
 }
 
+// ---- edge-edge mollifier ------------------------------------------------------------
+// The segment-segment distance is not C^1 where two edges turn parallel, so an
+// exact Newton step cannot converge through such a configuration. Every
+// edge-edge term is therefore scaled by m(c), c = |u x v|^2 with u, v the two
+// edge vectors: m = (2 - c/eps) c/eps for c < eps = 1e-3 |u_rest|^2 |v_rest|^2,
+// and 1 above (the mollifier of IPC, Li et al. 2020, whose barrier the paper
+// uses; the paper itself is silent on parallel edges). m is C^1 at c = eps.
+struct Mollifier {
+  bool on;              // c < eps, i.e. m < 1
+  double m, m1, m2;     // m, dm/dc, d2m/dc2
+  d3 u, v;
+};
+__device__ inline Mollifier ee_mollifier(const Dev& S, uint64_t key, const d3 X[4]) {
+  Mollifier M;
+  M.on = false;
+  M.m = 1.0;
+  M.m1 = M.m2 = 0.0;
+  M.u = X[1] - X[0];
+  M.v = X[3] - X[2];
+  if (key_kind(key) == 0) return M;
+  const double eps = 1e-3 * S.edge_l2[key_a(key)] * S.edge_l2[key_b(key)];
+  const d3 n = cross(M.u, M.v);
+  const double c = dot(n, n);
+  if (!(c < eps)) return M;
+  const double r = c / eps;
+  M.on = true;
+  M.m = (2.0 - r) * r;
+  M.m1 = (2.0 - 2.0 * r) / eps;
+  M.m2 = -2.0 / (eps * eps);
+  return M;
+}
+// grad c on the 12 stencil DOFs: c = |u|^2 |v|^2 - (u.v)^2 with u = X1 - X0,
+// v = X3 - X2, so dc/du = 2|v|^2 u - 2(u.v) v and dc/dv = 2|u|^2 v - 2(u.v) u
+__device__ inline void mollifier_grad_c(const Mollifier& M, double gc[12]) {
+  const double uu = dot(M.u, M.u), vv = dot(M.v, M.v), uv = dot(M.u, M.v);
+  const d3 gu = (2.0 * vv) * M.u - (2.0 * uv) * M.v;
+  const d3 gv = (2.0 * uu) * M.v - (2.0 * uv) * M.u;
+  const d3 g[4] = {-1.0 * gu, gu, -1.0 * gv, gv};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    gc[3 * k] = g[k].x;
+    gc[3 * k + 1] = g[k].y;
+    gc[3 * k + 2] = g[k].z;
+  }
+}
+// entry (r, c) of the Hessian of c on the 12 DOFs: with e_uu = 2|v|^2 I - 2 v v^T,
+// e_vv = 2|u|^2 I - 2 u u^T, e_uv = 4 u v^T - 2(u.v) I - 2 v u^T, e_vu = e_uv^T,
+// signed by the node's sign in u or v (X0, X2: -1; X1, X3: +1)
+__device__ inline double mollifier_hess_c(const Mollifier& M, int r, int c, double uu, double vv,
+                                          double uv) {
+  const int a = r / 3, i = r % 3, b = c / 3, j = c % 3;
+  const double sgn = ((a & 1) ? 1.0 : -1.0) * ((b & 1) ? 1.0 : -1.0);
+  const double u[3] = {M.u.x, M.u.y, M.u.z}, v[3] = {M.v.x, M.v.y, M.v.z};
+  const double dij = i == j ? 1.0 : 0.0;
+  double e;
+  if (a < 2 && b < 2) e = 2.0 * vv * dij - 2.0 * v[i] * v[j];
+  else if (a >= 2 && b >= 2) e = 2.0 * uu * dij - 2.0 * u[i] * u[j];
+  else if (a < 2) e = 4.0 * u[i] * v[j] - 2.0 * uv * dij - 2.0 * v[i] * u[j];
+  else e = 4.0 * u[j] * v[i] - 2.0 * uv * dij - 2.0 * v[j] * u[i];
+  return sgn * e;
+}
+
 // ---- derivatives of d^2 (hand-derived, per region) ----------------------------------
 // Variables are differences of stencil nodes: var_k = sum_n C[k][n] X[n] with C in
 // {-1,0,1}. f = d^2(vars); fk[k] = df/dvar_k; Fkl[k][l] = d2f/dvar_k dvar_l (3x3).
@@ -471,6 +533,16 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
     const double c2 = S.dhat + A.s[i];
     const double p1 = inA * A.sigma * dbar(d, S.dhat) + inAp * (-A.mu[i] + A.sigma * dbar(d, c2));
     const double p2 = inA * A.sigma * d2bar(d, S.dhat) + inAp * A.sigma * d2bar(d, c2);
+    // edge-edge mollifier: phi_EE = m phi, grad = m phi' grad d + phi m' grad c
+    const Mollifier M = ee_mollifier(S, key, X);
+    double e0 = 0.0, gc[12];
+    if (M.on) {
+      e0 = inA * A.sigma * bar(d, S.dhat) + inAp * (A.mu[i] * (c2 - d) + A.sigma * bar(d, c2));
+      mollifier_grad_c(M, gc);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) gc[k] = 0.0;
+    }
     // g2 = grad(d^2) on the 12 stencil DOFs
     double g2[12];
 #pragma unroll
@@ -480,8 +552,8 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
         if (V.C[k][nd] != 0) acc = acc + (double)V.C[k][nd] * V.fk[k];
       g2[3 * nd] = acc.x; g2[3 * nd + 1] = acc.y; g2[3 * nd + 2] = acc.z;
     }
-    const double cg = p1 / (2.0 * d);
-    // friction: normal force lambda = -phi'(d), normal and weights at x; the
+    const double cg = M.m * p1 / (2.0 * d), cm = e0 * M.m1;
+    // friction: normal force lambda = -m phi'(d), normal and weights at x; the
     // slip w against x^t; D = chi lambda f(|w|), grad = chi lambda a beta_k w,
     // Hess block (k, l) = chi lambda beta_k beta_l (a P + c w w^T)
     double beta[4] = {0, 0, 0, 0}, fk = 0.0, fa = 0.0, fcy = 0.0;
@@ -496,7 +568,7 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
       }
       nh = (1.0 / sqrt(dot(nv, nv))) * nv;
       w = tangent_slip(beta, X, Xt, nh);
-      const double lam = -p1;
+      const double lam = -M.m * p1;
       fk = A.chi * lam;
       const double y = sqrt(dot(w, w)), eh = A.eps_h;
       if (y < eh) {
@@ -521,8 +593,9 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
       pin[nd] = S.pinned[v[nd]] != 0;
       if (!pin[nd] && A.grad) {
         const double cf = fk * fa * beta[nd];
-        atomic_add3(A.grad, v[nd], d3{cg * g2[3 * nd] + cf * w.x, cg * g2[3 * nd + 1] + cf * w.y,
-                                      cg * g2[3 * nd + 2] + cf * w.z});
+        atomic_add3(A.grad, v[nd], d3{cg * g2[3 * nd] + cm * gc[3 * nd] + cf * w.x,
+                                      cg * g2[3 * nd + 1] + cm * gc[3 * nd + 1] + cf * w.y,
+                                      cg * g2[3 * nd + 2] + cm * gc[3 * nd + 2] + cf * w.z});
       }
     }
     if (!A.hess) continue;
@@ -544,6 +617,16 @@ __global__ void __launch_bounds__(128) k_contact_terms(Dev S, const double* __re
             const int r = 3 * nd + ii, c = 3 * md + jj;
             H[12 * r + c] = c1 * g2[r] * g2[c] + cc2 * h2;
           }
+    if (M.on) {
+      // m (phi'' grad d grad d^T + phi' Hess d) + phi' m' (grad d grad c^T + grad c grad d^T)
+      // + phi (m'' grad c grad c^T + m' Hess c)
+      const double uu = dot(M.u, M.u), vv = dot(M.v, M.v), uv = dot(M.u, M.v);
+      const double cx = p1 * M.m1 / (2.0 * d), cgg = e0 * M.m2, chc = e0 * M.m1;
+      for (int r = 0; r < 12; ++r)
+        for (int c = 0; c < 12; ++c)
+          H[12 * r + c] = M.m * H[12 * r + c] + cx * (g2[r] * gc[c] + gc[r] * g2[c]) +
+                          cgg * gc[r] * gc[c] + chc * mollifier_hess_c(M, r, c, uu, vv, uv);
+    }
     // symmetrise, project to PSD
     for (int r = 0; r < 12; ++r)
       for (int c = r + 1; c < 12; ++c) {
@@ -643,7 +726,7 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
     Region R;
     const double d = pair_distance(S, x, cand[i], v, X, R);
     if (d < S.dhat) {
-      e += sigma * bar(d, S.dhat);
+      e += ee_mollifier(S, cand[i], X).m * sigma * bar(d, S.dhat);
       cnt += 1.0;
     }
   }
@@ -653,7 +736,7 @@ __global__ void __launch_bounds__(NT) k_contact_energy(Dev S, const double* __re
     Region R;
     const double d = pair_distance(S, x, apk[i], v, X, R);
     const double c2 = S.dhat + aps[i];
-    e += apmu[i] * (c2 - d) + sigma * bar(d, c2);
+    e += ee_mollifier(S, apk[i], X).m * (apmu[i] * (c2 - d) + sigma * bar(d, c2));
   }
   // friction with the lagged weights, normals and forces
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < F.n; i += (int64_t)gridDim.x * NT) {

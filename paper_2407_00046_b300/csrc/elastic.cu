@@ -506,10 +506,12 @@ bal_status launch_elastic_assemble(Scene& S, const double* x, cudaStream_t st) {
   if (S.d.nnzL > 0) BAL_CUDA(cudaMemsetAsync(S.d.Lval, 0, sizeof(double) * 9 * S.d.nnzL, st));
   if (S.d.nt > 0) {
     // single-precision path: element eigensystems in FP32 (projected Hessian only)
+    if (S.ktime) cudaEventRecord(S.kaev[0], st);
     if (S.prm.precision == BAL_PREC_FP32 && S.project)
       k_elastic_hess<float><<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, 1);
     else
       k_elastic_hess<double><<<grid_for(S.d.nt, 128, kNumSM * 32), 128, 0, st>>>(S.d, x, S.project ? 1 : 0);
+    if (S.ktime) cudaEventRecord(S.kaev[1], st);
     ::bal::note_launch();
     BAL_LAUNCH_CHECK();
   }

@@ -45,41 +45,6 @@ __global__ void k_finish(const double* __restrict__ partials, int n, double* out
   if (threadIdx.x == 0) *out = acc;
 }
 
-// ---- contact blocks: heads of equal-key runs, then per-run sums -------------------
-__global__ void k_iota(int32_t* a, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    a[i] = (int32_t)i;
-}
-__global__ void k_heads(const uint64_t* __restrict__ k, int64_t n, int32_t* __restrict__ head) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    head[i] = (k[i] != ~0ull && (i == 0 || k[i] != k[i - 1])) ? 1 : 0;
-}
-__global__ void k_segsum(const uint64_t* __restrict__ k, const int32_t* __restrict__ idx,
-                         const double* __restrict__ vals, const int32_t* __restrict__ head,
-                         const int32_t* __restrict__ pos, int64_t n, int32_t* __restrict__ crow,
-                         int32_t* __restrict__ ccol, double* __restrict__ cval) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (!head[i]) continue;
-    const uint64_t key = k[i];
-    double acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-    for (int64_t j = i; j < n && k[j] == key; ++j) {
-      const double* v = vals + 9 * (int64_t)idx[j];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) acc[c] += v[c];
-    }
-    const int32_t o = pos[i];
-    crow[o] = (int32_t)(key >> 32);
-    ccol[o] = (int32_t)(key & 0xffffffffu);
-#pragma unroll
-    for (int c = 0; c < 9; ++c) cval[9 * (int64_t)o + c] = acc[c];
-  }
-}
-
 __global__ void k_dinv(Dev S) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < S.nv; v += gridDim.x * blockDim.x) {
     const double* a = S.D + 9 * (int64_t)v;
@@ -682,48 +647,6 @@ bal_status finish_reduce_offset(Scene& S, int offset, int n, int slot, RedOp op,
   return BAL_OK;
 }
 
-bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
-  S.nnzC = 0;
-  if (n_emit <= 0) return BAL_OK;
-  BAL_TRY(buf_reserve(S.emit_keys_alt, sizeof(uint64_t) * n_emit));
-  BAL_TRY(buf_reserve(S.emit_idx, sizeof(int32_t) * n_emit));
-  BAL_TRY(buf_reserve(S.emit_idx_alt, sizeof(int32_t) * n_emit));
-  BAL_TRY(buf_reserve(S.seg_head, sizeof(int32_t) * (n_emit + 1)));
-  BAL_TRY(buf_reserve(S.seg_pos, sizeof(int32_t) * (n_emit + 1)));
-  k_iota<<<grid_for(n_emit), kThreads, 0, st>>>(S.emit_idx.as<int32_t>(), n_emit);
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
-  cub::DoubleBuffer<uint64_t> dk(S.emit_keys.as<uint64_t>(), S.emit_keys_alt.as<uint64_t>());
-  cub::DoubleBuffer<int32_t> dv(S.emit_idx.as<int32_t>(), S.emit_idx_alt.as<int32_t>());
-  size_t tmp = 0;
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, n_emit, 0, 64, st));
-  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, n_emit, 0, 64, st));
-  int32_t* head = S.seg_head.as<int32_t>();
-  int32_t* pos = S.seg_pos.as<int32_t>();
-  k_heads<<<grid_for(n_emit), kThreads, 0, st>>>(dk.Current(), n_emit, head);
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
-  BAL_CUDA(cudaMemsetAsync(head + n_emit, 0, sizeof(int32_t), st));
-  tmp = 0;
-  BAL_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, head, pos, n_emit + 1, st));
-  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceScan::ExclusiveSum(S.cub_tmp.p, tmp, head, pos, n_emit + 1, st));
-  int32_t nC = 0;
-  BAL_CUDA(cudaMemcpyAsync(&nC, pos + n_emit, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  BAL_CUDA(cudaStreamSynchronize(st));
-  BAL_TRY(buf_reserve(S.C_row, sizeof(int32_t) * (nC + 1)));
-  BAL_TRY(buf_reserve(S.C_col, sizeof(int32_t) * (nC + 1)));
-  BAL_TRY(buf_reserve(S.C_val, sizeof(double) * 9 * (nC + 1)));
-  k_segsum<<<grid_for(n_emit), kThreads, 0, st>>>(dk.Current(), dv.Current(), S.emit_vals.as<double>(),
-                                                 head, pos, n_emit, S.C_row.as<int32_t>(),
-                                                 S.C_col.as<int32_t>(), S.C_val.as<double>());
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
-  S.nnzC = nC;
-  return BAL_OK;
-}
-
 template <typename T>
 static bal_status compact_t(Scene& S, const T* in, const uint8_t* flag, int64_t n, T* out,
                             int64_t* nsel, cudaStream_t st) {
@@ -816,9 +739,29 @@ bal_status residual_fp64(Scene& S, const double* b, const double* x, double* r, 
   return BAL_OK;
 }
 
+// FP64 value of the quadratic model f(x) = x^T H x / 2 - b^T x from x and its
+// residual r = b - H x: f = -(b.x + r.x) / 2. f(x) - f(x*) = |x - x*|_H^2 / 2, so
+// f falls exactly when the error falls in the energy norm, the norm CG reduces.
+static bal_status quad_model(Scene& S, int64_t n3, const double* b, const double* r, const double* x,
+                             double* f, cudaStream_t st) {
+  BAL_TRY(launch_dot(S, n3, b, x, 30, st));
+  BAL_TRY(launch_dot(S, n3, r, x, 31, st));
+  double v[2];
+  BAL_CUDA(cudaMemcpyAsync(v, S.scal + 30, sizeof(v), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaStreamSynchronize(st));
+  *f = -0.5 * (v[0] + v[1]);
+  return BAL_OK;
+}
+
 // FP32 inner PCG on the FP32 copy of H, FP64 outer residual and correction
 // (iterative refinement): r = b - H x (FP64), solve H e = r/||r|| in FP32 to
-// mixed_inner_tol, x += ||r|| e, repeat until ||r|| <= tol ||r_0||.
+// mixed_inner_tol, trial x + ||r|| e, repeat until ||r|| <= tol ||r_0||.
+// A pass is kept if it lowers the FP64 quadratic model (the energy-norm
+// error, which CG reduces monotonically even while ||r||_2 rises) or the FP64
+// residual (near convergence the model's decrease, ~||e||_H^2, is below the
+// rounding of f itself); a pass that lowers neither is rolled back and ends
+// the solve. On exit without convergence x is the iterate with the smallest
+// FP64 residual seen.
 static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, int max_it,
                             bal_solve_info* info, cudaStream_t st) {
   if (!S.f32_valid) {
@@ -826,20 +769,15 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     S.f32_valid = true;
   }
   const int64_t n3 = 3 * (int64_t)S.d.nv;
-  BAL_TRY(spmv(S, x, S.pcg_q, st));
-  k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
+  double* xtrial = S.pcg_p;   // FP64 work vectors the FP64 solvers own; free here
+  double* xbest = S.pcg_z;
   double rn, bn;
-  BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
-  {
-    double res[2];
-    BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
-    BAL_CUDA(cudaStreamSynchronize(st));
-    rn = sqrt(res[0]);
-    bn = sqrt(res[1]);
-  }
+  BAL_TRY(residual_fp64(S, b, x, S.pcg_r, &rn, &bn, st));
   const double r0 = rn;
+  double fx;
+  BAL_TRY(quad_model(S, n3, b, S.pcg_r, x, &fx, st));
+  double best_rn = rn;
+  bool best_is_x = true;
   int total = 0, passes = 0;
   bool converged = rn <= tol * r0 || rn == 0.0;
   const Sys<float> A = sys32(S);
@@ -855,26 +793,41 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
                             S.prm.pcg_stall_window, &h, st));
     total += h.it;
     passes += 1;
-    k_refine_update<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, S.x32, x);
+    if (h.it == 0) break;
+    BAL_CUDA(cudaMemcpyAsync(xtrial, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+    k_refine_update<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, S.x32, xtrial);
     ::bal::note_launch();
     BAL_LAUNCH_CHECK();
-    BAL_TRY(spmv(S, x, S.pcg_q, st));
-    k_sub<<<grid_for(n3), kThreads, 0, st>>>(n3, b, S.pcg_q, S.pcg_r);
-    ::bal::note_launch();
-    BAL_LAUNCH_CHECK();
-    BAL_TRY(launch_residual_norm(S, b, S.pcg_q, st));
-    double res[2];
-    BAL_CUDA(cudaMemcpyAsync(res, S.scal + 8, sizeof(res), cudaMemcpyDeviceToHost, st));
-    BAL_CUDA(cudaStreamSynchronize(st));
-    const double rn_new = sqrt(res[0]);
+    double rn_new, bn2;
+    BAL_TRY(residual_fp64(S, b, xtrial, S.pcg_r, &rn_new, &bn2, st));
     if (!std::isfinite(rn_new)) {
       set_error("mixed pcg: non-finite residual after refinement pass %d", passes);
       return BAL_ERR_NAN;
     }
-    const bool progress = rn_new < 0.99 * rn;
+    double f_new;
+    BAL_TRY(quad_model(S, n3, b, S.pcg_r, xtrial, &f_new, st));
+    if (!(f_new < fx) && !(rn_new < rn)) {
+      // neither the energy-norm error (f) nor the FP64 residual fell: roll the
+      // pass back (x and its residual norm stay those of the previous pass;
+      // S.pcg_r is not used after the loop)
+      break;
+    }
+    if (best_is_x) {   // x is about to change and holds the smallest residual so far
+      BAL_CUDA(cudaMemcpyAsync(xbest, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+      best_is_x = false;
+    }
+    BAL_CUDA(cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+    fx = f_new;
     rn = rn_new;
+    if (rn <= best_rn) {
+      best_rn = rn;
+      best_is_x = true;
+    }
     converged = rn <= tol * r0;
-    if (!progress || h.it == 0) break;
+  }
+  if (!converged && !best_is_x) {
+    BAL_CUDA(cudaMemcpyAsync(x, xbest, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+    rn = best_rn;
   }
   if (info) {
     info->iters = total;

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kNaThreads) k_na_init(NaMat A, double* S, cons
     const double tbb = na_sum(part + 2 * gridDim.x, gridDim.x);
     if (threadIdx.x == 0) {
       P->rz = trz;
-      P->r0norm = P->rnorm = P->best = sqrt(trr);
+      P->r0norm = P->rnorm = sqrt(trr);
+      P->best = sqrt(fmax(trz, 0.0));   // stagnation is judged on the preconditioned norm
       P->bnorm = sqrt(tbb);
       P->tol_abs = tol * P->r0norm;
       P->it = P->best_it = 0;
@@ -242,10 +243,11 @@ __global__ void __launch_bounds__(kNaThreads) k_na_update(NaMat A, double* S, do
     if (threadIdx.x == 0) {
       const int it = P->it + 1;
       const double rn = sqrt(trr);
+      const double pn = sqrt(fmax(trz, 0.0));   // preconditioned residual norm
       P->it = it;
       P->rnorm = rn;
-      if (rn < P->best) {
-        P->best = rn;
+      if (pn < P->best) {
+        P->best = pn;
         P->best_it = it;
       }
       if (!isfinite(rn)) P->done = 2;

@@ -52,6 +52,7 @@ struct Dev {
   const int32_t *tets = nullptr, *tris = nullptr, *edges = nullptr, *surf = nullptr;
   const uint8_t* pinned = nullptr;
   const double *Dm_inv = nullptr, *vol = nullptr, *mu = nullptr, *lam = nullptr, *mass = nullptr;
+  const double* edge_l2 = nullptr;   // [ne] rest squared length of each surface edge (EE mollifier)
   // static lower pattern: CSR + per-block row, element -> slot map
   const int32_t *L_row_ptr = nullptr, *L_col = nullptr, *L_row = nullptr;
   const int32_t* tet_slot = nullptr;  // [nt][6]: 2*slot + (1 if the stored block is the transpose)
@@ -89,6 +90,7 @@ struct Scene {
   // padding entries point at zero blocks.
   int32_t n_slices = 0;
   bool sell_built = false;
+  int32_t sell_window = 0;     // spmv_window the layout was built for
   Buf sell_offR, sell_offT;   // [n_slices+1] entry offsets (multiples of 32)
   Buf sell_Rcol;              // [offR[n]] column of each row-side entry
   Buf sell_Tpos, sell_Tsrc;   // [offT[n]] value position / source row of each column-side entry
@@ -113,7 +115,10 @@ struct Scene {
   std::vector<double> E_h, nu_h;
 
   // contact emission + sort scratch
-  Buf emit_keys, emit_keys_alt, emit_idx, emit_idx_alt, emit_vals, seg_head, seg_pos;
+  Buf emit_keys, emit_vals;      // contact blocks as emitted: [n][6] keys, [n][6][9] values
+  // duplicate-block merge (segreduce.cu): per-row counts / offsets, buckets,
+  // ordered record indices, distinct-column counts / offsets, scan tile sums
+  Buf cm_cnt, cm_off, cm_bucket, cm_sorted, cm_ucnt, cm_uoff, scan_aux;
   Buf cub_tmp;
 
   // broad phase scratch
@@ -158,6 +163,12 @@ struct Scene {
   cudaEvent_t kev[2 * kTimedPerChunk] = {};
   double kt_ms = 0;
   int64_t kt_n = 0;
+  // the same switch times the assembly: the element Hessian kernel alone
+  // (events 0, 1) and the whole assembly (events 2, 3: elastic, contact
+  // stencils, duplicate-block merge, D^-1) of every assemble call
+  cudaEvent_t kaev[4] = {};
+  double ka_elastic_ms = 0, ka_total_ms = 0;
+  int64_t ka_n = 0;
 
   // AL state of the current time step (host copy is authoritative)
   bool step_active = false;
@@ -240,6 +251,7 @@ bal_status lbvh_candidates(Scene& S, const double* x, const double* dir, double 
 
 // ---- matrix.cu -----------------------------------------------------------------
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
+bal_status scan_i32(Scene& S, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 bal_status launch_dinv(Scene& S, cudaStream_t st);
 bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
 bal_status spmv32(Scene& S, const float* v, float* y, cudaStream_t st);

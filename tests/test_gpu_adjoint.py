@@ -122,14 +122,14 @@ def test_adjoint_matches_central_fd_with_frozen_al_state():
     frozen = [c[3] for c in ck]
     rng = np.random.default_rng(1)
     w = rng.choice([-1.0, 1.0], size=sc.n_tets)
-    eps = 1e-4
+    eps = 1e-6                                   # relative step in E, as for v0
     vals = []
     for sgn in (1, -1):
         xs, _ = _rollout(S, sc, steps, frozen, E=sc.E * (1 + sgn * eps * w))
         vals.append(float(centroid_loss(xs, mass, body, target)))
     fd = (vals[0] - vals[1]) / (2 * eps)
     adj = float((E.grad * T(sc.E) * T(w)).sum())
-    assert adj == pytest.approx(fd, rel=1e-4)
+    assert adj == pytest.approx(fd, rel=1e-5)
     u = np.zeros_like(sc.V0)
     u[sc.body == 0] = rng.normal(size=(int((sc.body == 0).sum()), 3))
     vals = []

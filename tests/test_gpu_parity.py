@@ -7,6 +7,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import bal as obal  # noqa: E402
+from oracle import contact  # noqa: E402
 from oracle import system  # noqa: E402
 from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 
@@ -56,6 +57,10 @@ def test_assembly_matches_oracle(contact_case, with_ap):
     view = S.assemble_hessian(T(x), g)
     Hg, lam_g, _ = gpu_hessian(S, view)
     m, y, ps = oracle_state(sc, x, sigma, ap)
+    # the perturbed lattices put many edge-edge pairs inside the mollified zone
+    X4 = x[contact.stencil_nodes(ps.keys, sc)]
+    mol = contact.mollifier(X4, contact.ee_eps(ps.keys, sc), derivs=False)
+    assert np.sum((mol > 0.0) & (mol < 1.0)) >= 10
     g_or = system.gradient(m, x, y, ps, sigma).ravel()
     H_or, lam_or = system.hessian(m, x, y, ps, sigma, with_lambda=True)
     gerr = np.abs(g.cpu().numpy() - g_or).max() / np.abs(g_or).max()
@@ -220,3 +225,56 @@ def test_warm_start_solves_the_grouped_system(contact_case):
         assert res <= 1.05e-9 * max(1.0, r0_over_b), (res, info)
     finally:
         S.set_params(precond=bal.PRECOND_BJ)
+
+
+def _fine_on_coarse():
+    """A 6^3-cell cube (small vertex ids) resting 0.4 mm above the top face of a
+    single-cell box (large vertex ids): every point of the fine bottom face
+    is in contact with one of two big triangles, so the rows of the box's
+    top vertices collect many emitted blocks (more than 32) with long runs of
+    the same column."""
+    from paper_2407_00046_b300.scenes import lattice_box, merge_bodies
+    Xf, Tf = lattice_box(6, 6, 6, (0.03, 0.03, 0.03))
+    Xc, Tc = lattice_box(1, 1, 1, (0.06, 0.02, 0.06))
+    Xf = Xf + np.array([0.012, 0.0204, 0.012])
+    rng = np.random.default_rng(4)
+    Xf = Xf + 2e-5 * rng.normal(size=Xf.shape)
+    return merge_bodies("fine_on_coarse", [dict(X=Xf, tets=Tf, E=1e5),
+                                           dict(X=Xc, tets=Tc, E=1e6,
+                                                pinned=Xc[:, 1] <= 1e-12)])
+
+
+def test_contact_merge_with_long_rows_matches_oracle():
+    sc = _fine_on_coarse()
+    m = system.make_model(sc)
+    keys, d = obal.active_pairs(m, sc.X)
+    assert len(keys) > 40 and d.min() > 0
+    S = bal.Scene(sc, bal.default_params())
+    S.step_begin(T(sc.X), T(sc.V0))
+    sigma = 2.0
+    S.set_al_state(sigma, sigma)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    view = S.assemble_hessian(T(sc.X), g)
+    Hg, _, parts = gpu_hessian(S, view)
+    # rows of the coarse box with more than 32 contact records (6 emitted per pair)
+    nodes = contact.stencil_nodes(keys, sc)
+    emitted = {}
+    for st in nodes:
+        for a in range(4):
+            for b in range(a):
+                r, c = max(st[a], st[b]), min(st[a], st[b])
+                if r != c and not (sc.pinned[r] or sc.pinned[c]):
+                    emitted[r] = emitted.get(r, 0) + 1
+    assert max(emitted.values()) > 64
+    # C sorted by (row, col) without duplicates
+    rc = parts["Cr"].astype(np.int64) * sc.n_verts + parts["Cc"]
+    assert np.all(np.diff(rc) > 0) and np.all(parts["Cr"] > parts["Cc"])
+    y = system.inertia_target(m, sc.X, sc.V0)
+    ps = obal.make_pairset(m, sc.X, keys, {}, sigma)
+    H_or = system.hessian(m, sc.X, y, ps, sigma)
+    herr = np.abs((Hg - H_or).toarray()).max() / np.abs(H_or.toarray()).max()
+    assert herr < HESS_TOL, herr
+    # bit-reproducible merge: a second assembly gives identical blocks
+    view2 = S.assemble_hessian(T(sc.X), g)
+    _, _, parts2 = gpu_hessian(S, view2)
+    assert np.array_equal(parts["Cv"], parts2["Cv"]) and np.array_equal(parts["Cr"], parts2["Cr"])

@@ -63,3 +63,40 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(bal.BalError, match="BAL_NOALLOC_MAX_VERTS"):
         bal.pcg_solve_noalloc(D, e, e, torch.zeros(0, dtype=torch.float64, device="cuda"), v, v,
                               1e-8, 10)
+
+
+def test_noalloc_warm_start_cap_empty_lower_part_and_singular_block():
+    """A nonzero initial guess and an iteration cap give the regular solve's
+    iterate; a matrix without lower blocks solves block by block; a singular
+    diagonal block is reported as BAL_ERR_NAN."""
+    S, D, rows, cols, vals = _assembled()
+    n = 3 * S.nv
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    b = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+    x0 = 1e-3 * torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+    # warm start to convergence
+    ref, sol = x0.clone(), x0.clone()
+    info_ref = S.pcg_solve(b, ref, TOL, 20000)
+    info = bal.pcg_solve_noalloc(D, rows, cols, vals, b, sol, TOL, 20000)
+    assert info["converged"] == 1 and info_ref["converged"] == 1
+    assert float((sol - ref).norm() / ref.norm()) < 1e-6
+    # iteration cap: the same count and nearly the same iterate (atomic sums differ in rounding)
+    ref, sol = x0.clone(), x0.clone()
+    info_ref = S.pcg_solve(b, ref, 1e-14, 7)
+    info = bal.pcg_solve_noalloc(D, rows, cols, vals, b, sol, 1e-14, 7)
+    assert info["iters"] == info_ref["iters"] == 7 and info["converged"] == 0
+    assert float((sol - ref).norm() / ref.norm()) < 1e-9
+    # no lower blocks: H = D, one PCG iteration solves each 3x3 system
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    ev = torch.zeros(0, dtype=torch.float64, device="cuda")
+    sol = torch.zeros_like(b)
+    info = bal.pcg_solve_noalloc(D, e, e, ev, b, sol, 1e-12, 10)
+    assert info["converged"] == 1 and info["iters"] <= 1
+    Db = D.view(-1, 3, 3)
+    res = b.view(-1, 3) - torch.einsum("nij,nj->ni", Db, sol.view(-1, 3))
+    assert float(res.norm() / b.norm()) <= 1e-12
+    # a singular diagonal block: D^-1 is not finite
+    Ds = D.clone()
+    Ds[:9] = 0.0
+    with pytest.raises(bal.BalError, match="NAN"):
+        bal.pcg_solve_noalloc(Ds, e, e, ev, b, torch.zeros_like(b), 1e-12, 10)
