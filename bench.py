@@ -1,19 +1,22 @@
-"""Benchmark of the BAL inexact Newton-PCG time step on one B300.
+"""Benchmark of the BAL inexact Newton-PCG path on one B300.
 
 Workload (default): the heterogeneous net scene -- an interlocked torus-link
 chain net (E = 1 GPa, border links pinned) under four spiked spherical shells
 (E = 5e5 Pa) dropped from 2 cm, ~1.77M tets, h = 1/30 s, dhat = 1e-3 m,
 synthetic and seeded (it stands in for the paper's "Puffer Balls on Nets",
-Table 1). A step is one full time step (Algorithm 1 until convergence: contact
-detection, assembly, PCG solves, line searches). W warm-up steps (the shells
-reach the net), then K timed steps.
+Table 1).
 
-Prints one JSON line. value = PCG iterations per second over the timed steps
-(whole step time, all ranks); ms_per_step = wall time per time step. The
-matrix is larger than L2 at this size, so no L2 flush is inserted.
-`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
-Multi-GPU: independent replicas of the scene, one per rank (weak scaling; the
-path has no collective).
+First --time-steps whole time steps are run from the initial state to
+convergence of Algorithm 1, each timed with CUDA events (the ms-per-time-step
+half of the metric; reported under "time_steps"). Then the benchmark steps:
+W warm-up and K timed Algorithm 1 iterations of the following time step(s),
+each one pass of the whole hot path (contact detection, projected-Hessian
+assembly, PCG solve, step bound and line search, AL update). value = PCG
+iterations per second over the K timed iterations (all ranks); ms_per_step =
+ms per Algorithm 1 iteration. The matrix is larger than L2 at this size, so no
+L2 flush is inserted. `--impl reference` times the FP64 CPU oracle on a bounded
+sample instead. Multi-GPU: independent replicas of the scene, one per rank
+(weak scaling; the path has no collective).
 """
 import argparse
 import json
@@ -95,10 +98,12 @@ class Clocks:
         return out
 
 
-# FP64 FMA throughput of this machine's B300 (dependent-chain-free FMA probe, 1.13
-# TFLOP/s; 148 SMs x 2 DFMA/clk x 2 flop x ~1.94 GHz); MEASURED_PEAKS.json has no
-# FP64 figure.
-FP64_PEAK_TFLOPS = 1.128
+# FP64 operations per tet of k_elastic_hess<double> (projected Hessian: F,
+# signed SVD by 3x3 Jacobi, the analytic eigensystem of the 9x9 dP/dF, the
+# 12x12 block and its slot scatter): ncu SASS counters of one launch on the
+# chain-net workload, 2 x DFMA + DADD + DMUL per tet
+# (profiles/k_elastic_hess_chain_net_shells.md).
+ELASTIC_HESS_FLOP_PER_TET = 2600.0
 
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2, "fp32": 3}     # bal_precision values
@@ -153,18 +158,47 @@ def ncu_traffic(precision, scene):
     return rec["bytes"]
 
 
-def roofline_entry(precision, kname, achieved, peak, peak_kind, byts, ms, n, nv, nnzL, nnzC, traffic=None):
+def roofline_entry(precision, kname, achieved, peak, peak_kind, byts, ms, n, nv, nnzL, nnzC, traffic=None,
+                   fp64_peak=None):
     out = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
            "traffic": traffic, "bytes_per_launch": byts, "ms_per_launch": round(ms, 5),
            "timed_launches": n, "nnz_L": nnzL, "nnz_C_last": nnzC}
-    if precision == "fp64":
+    if precision == "fp64" and fp64_peak:
         flops = 36.0 * (nnzL + nnzC)
         tf = flops / (ms * 1e-3) / 1e12
         out["alu"] = {"bound": "alu", "unit": "FP64 TFLOP/s", "achieved": round(tf, 4),
-                      "peak": FP64_PEAK_TFLOPS, "frac": round(tf / FP64_PEAK_TFLOPS, 4),
-                      "peak_kind": "measured (FP64 FMA probe, 148 SMs x 2 DFMA/clk)"}
+                      "peak": round(fp64_peak, 4), "frac": round(tf / fp64_peak, 4),
+                      "peak_kind": "measured in this run (bal_fp64_fma_rate)"}
     return out
+
+
+def assembly_bytes(n_tets, nv, nnzL, n_pairs):
+    """Algorithmic bytes of one assembly: per tet its 4 indices, D_m^-1 (9 f64)
+    and V, mu, lambda; positions read once; the diagonal and static lower
+    blocks written once (f64); per contact pair its key and 10 emitted
+    blocks (4 diagonal, 6 off-diagonal) written and read once by the merge."""
+    return n_tets * (16 + 72 + 24) + nv * 24 + (nv + nnzL) * 72 + n_pairs * (8 + 2 * 10 * 72)
+
+
+def assembly_roofline(n_tets, nv, nnzL, n_pairs, elastic_ms, total_ms, n, fp64_peak, hbm_peak, peak_kind):
+    """The element Hessian kernel against the measured FP64 FMA rate (it is
+    bound by the FP64 pipe on B300), and the whole assembly's algorithmic
+    bytes against the measured HBM copy bandwidth."""
+    if n == 0:
+        return None
+    e_ms, t_ms = elastic_ms / n, total_ms / n
+    tf = ELASTIC_HESS_FLOP_PER_TET * n_tets / (e_ms * 1e-3) / 1e12
+    byts = assembly_bytes(n_tets, nv, nnzL, n_pairs)
+    gbs = byts / (t_ms * 1e-3) / 1e9
+    return {"kernel": "k_elastic_hess<double>", "bound": "alu", "unit": "FP64 TFLOP/s",
+            "achieved": round(tf, 4), "peak": round(fp64_peak, 4), "frac": round(tf / fp64_peak, 4),
+            "peak_kind": "measured in this run (bal_fp64_fma_rate)", "ms_per_launch": round(e_ms, 4),
+            "flop_per_tet": ELASTIC_HESS_FLOP_PER_TET, "timed_assemblies": n,
+            "hbm": {"what": "whole assembly (element + contact stencils, duplicate merge, D^-1)",
+                    "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(gbs / hbm_peak, 4), "peak_kind": peak_kind, "bytes": byts,
+                    "ms_per_assembly": round(t_ms, 4), "contact_pairs_last": n_pairs}}
 
 
 def run_pcg_only(args):
@@ -179,7 +213,8 @@ def run_pcg_only(args):
     params = bal.default_params(pcg_stall_window=1 << 30,
                                 precision=PRECISIONS[args.precision],
                                 broad_phase=BROAD_PHASES[args.broad_phase],
-                                mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0)
+                                mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0,
+                                spmv_window=args.spmv_window)
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
     v = torch.tensor(sc.V0, dtype=torch.float64, device=dev)
@@ -222,9 +257,9 @@ def run_pcg_only(args):
 def _scene_params(args, bal, **kw):
     return bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
                               newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
-                              pcg_max_iter=30000, precision=PRECISIONS[args.precision],
+                              pcg_max_iter=args.pcg_max, precision=PRECISIONS[args.precision],
                               precond=PRECONDS[args.precond], step_mode=STEP_MODES[args.step_mode],
-                              broad_phase=BROAD_PHASES[args.broad_phase], **kw)
+                              broad_phase=BROAD_PHASES[args.broad_phase], spmv_window=args.spmv_window, **kw)
 
 
 def run_adjoint(args):
@@ -324,7 +359,20 @@ def reduce_over_ranks(ms, e2e_ms, pcg_iters, e2e_iters, world, dev=None):
     return float(mx[0]), float(mx[1]), float(sm[2]), float(sm[3])
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
 def run_ours(args, rank, world):
+    """Time steps of the workload to convergence from its initial state (each
+    one timed with CUDA events: the ms-per-time-step half of the metric), then
+    the benchmark proper: W warm-up and K timed Algorithm 1 iterations of the
+    following time step(s) in contact. One bench step = one Algorithm 1
+    iteration = one pass of the whole hot path (contact detection, assembly of
+    the projected Hessian, PCG solve, step bound and line search, AL update);
+    when a time step converges inside the run the next one begins (v update,
+    new inertia target and sigma0) and the iterations continue."""
     import torch
     from paper_2407_00046_b300 import bal, build, scenes
 
@@ -332,87 +380,105 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     sc = scenes.scene_by_name(args.scene)
-    params = bal.default_params(pcg_tol=args.pcg_tol, newton_tol=args.newton_tol,
-                                newton_max_iter=args.newton_max, pcg_stall_window=args.pcg_stall,
-                                pcg_max_iter=30000,
-                                precision=PRECISIONS[args.precision],
-                                precond=PRECONDS[args.precond], warm_tol=args.warm_tol,
-                                warm_max_iter=args.warm_iters,
-                                step_mode=STEP_MODES[args.step_mode],
-                                broad_phase=BROAD_PHASES[args.broad_phase],
-                                al_mode=AL_MODES[args.al_mode],
-                                pcg_tol_mode=PCG_TOL_MODES[args.pcg_tol_mode],
-                                friction=args.friction)
+    params = _scene_params(args, bal, warm_tol=args.warm_tol, warm_max_iter=args.warm_iters,
+                           al_mode=AL_MODES[args.al_mode], pcg_tol_mode=PCG_TOL_MODES[args.pcg_tol_mode],
+                           friction=args.friction, sigma_literal_max=int(args.sigma_rule == "printed"))
     S = bal.Scene(sc, params, pair_capacity=1 << 22)
     stream = torch.cuda.current_stream()
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
     v = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
-    log = []
 
-    def progress(tag, info):
+    def progress(tag, info, ms):
         print(f"[bench] {tag}: status {info['status']} newton {info['newton_iters']} pcg "
               f"{info['pcg_iters_total']} max|A| {info['max_active']} min d {info['min_distance']:.3e} "
-              f"ms {info['ms_total']:.0f} (asm {info['ms_assemble']:.0f} solve {info['ms_solve']:.0f} "
-              f"ls {info['ms_line_search']:.0f} contact {info['ms_contact']:.0f})",
+              f"sigma {info['sigma_final']:.4g} ms {ms:.0f} (asm {info['ms_assemble']:.0f} solve "
+              f"{info['ms_solve']:.0f} ls {info['ms_line_search']:.0f} contact {info['ms_contact']:.0f})",
               file=sys.stderr, flush=True)
 
-    for w in range(args.warmup):
-        log.append(S.time_step(x, v, check=False))
-        progress(f"warmup {w}", log[-1])
-    x0, v0 = x.clone(), v.clone()
+    # 1. whole time steps to convergence (Newton cap --newton-max), one by one
+    time_steps = []
+    for k in range(args.time_steps):
+        e0, e1 = _events()
+        e0.record(stream)
+        info = S.time_step(x, v, stream=stream, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        progress(f"time step {k}", info, ms)
+        time_steps.append({"step": k, "status": info["status"], "converged": int(info["converged"]),
+                           "ms": round(ms, 1), "newton_iters": info["newton_iters"],
+                           "pcg_iters": info["pcg_iters_total"], "max_active": info["max_active"],
+                           "min_distance": info["min_distance"], "sigma0": info["sigma0"],
+                           "sigma_final": info["sigma_final"],
+                           "phase_ms": {kk: round(info[kk], 1) for kk in
+                                        ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")}})
+
+    # 2. Algorithm 1 iterations of the next time step(s)
+    S.step_begin(x, v, stream=stream)
+    state = {"time_steps_done": 0}
+
+    def alg1_iteration(xx):
+        ni = S.newton_step(xx, stream=stream, check=False)
+        if ni["status"] not in (0, 7):       # OK, or a line search below alpha_min (reported)
+            raise RuntimeError(f"Algorithm 1 iteration failed: status {ni['status']}: {bal.last_error()}")
+        if ni["converged"]:                  # the time step is over: start the next one
+            S.step_end(xx, v, stream=stream)
+            S.step_begin(xx, v, stream=stream)
+            state["time_steps_done"] += 1
+        return ni
+
+    for _ in range(args.warmup):
+        alg1_iteration(x)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events()
     timed = []
     launches0 = bal.launch_count()
     S.kernel_timing(True)
     with Clocks(dev.index) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            timed.append(S.time_step(x, v, check=False))
+            timed.append(alg1_iteration(x))
         e1.record(stream)
         torch.cuda.synchronize()
     launches = bal.launch_count() - launches0
     k_ms, k_n = S.kernel_timing(False)
-    for k, t in enumerate(timed):
-        progress(f"timed {k}", t)
+    a_el_ms, a_tot_ms, a_n = S.assembly_timing()
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    pcg_iters = sum(t["pcg_iters_total"] for t in timed)
-    newton = sum(t["newton_iters"] for t in timed)
+    pcg_iters = sum(t["pcg_iters"] for t in timed)
 
-    # end to end through the public API with host buffers (same steps again)
-    xh = x0.cpu().pin_memory()
-    vh = v0.cpu().pin_memory()
-    xd, vd = torch.empty_like(x0), torch.empty_like(v0)
+    # end to end through the public API with host buffers: every iteration
+    # copies its input positions from pinned host memory and its result back
+    xh = x.cpu().pin_memory()
     torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0, f1 = _events()
     f0.record(stream)
     e2e_iters = 0
     for _ in range(args.steps):
-        xd.copy_(xh, non_blocking=True)
-        vd.copy_(vh, non_blocking=True)
-        info = S.time_step(xd, vd, check=False)
-        e2e_iters += info["pcg_iters_total"]
-        xh.copy_(xd, non_blocking=True)
-        vh.copy_(vd, non_blocking=True)
+        x.copy_(xh, non_blocking=True)
+        e2e_iters += alg1_iteration(x)["pcg_iters"]
+        xh.copy_(x, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
 
-    # roofline of the dominant kernel: the SpMV kernel of each PCG iteration,
-    # timed per launch with CUDA events on the solve stream during the timed region
+    # roofline of the dominant kernel: the SpMV of every PCG iteration, timed
+    # per launch with CUDA events on the solve stream during the timed region
     view = S.assemble_hessian(x)
     nv, nnzL, nnzC = sc.n_verts, view["nnz_L"], view["nnz_C"]
     kname, byts = spmv_kernel_bytes(args.precision, nv, nnzL, nnzC)
     spmv_ms = k_ms / max(k_n, 1)
     peak, peak_kind = peaks()
     achieved = byts / (spmv_ms * 1e-3) / 1e9
+    fp64_peak = bal.fp64_fma_rate(stream=stream)
+    max_pairs = max((t["n_active"] for t in timed), default=0)
     # PCG-only iteration rate on the same system (fixed iteration count)
     rhs = torch.randn(3 * nv, dtype=torch.float64, device=dev)
     sol = torch.zeros_like(rhs)
+    keep = S.get_params()
     S.set_params(pcg_stall_window=1 << 30)
     S.pcg_solve(rhs, sol, 0.0, 10)
     sol.zero_()
@@ -421,6 +487,7 @@ def run_ours(args, rank, world):
     pi = S.pcg_solve(rhs, sol, 0.0, 200)
     torch.cuda.synchronize()
     pcg_only = pi["iters"] / (time.perf_counter() - p0)
+    S.set_params(keep)
     forms = precision_forms(S, sc, dev, args) if not args.no_forms else None
 
     ms, e2e_ms, pcg_iters, e2e_iters = reduce_over_ranks(ms, e2e_ms, pcg_iters, e2e_iters, world, dev)
@@ -428,6 +495,8 @@ def run_ours(args, rank, world):
         return None
     value = pcg_iters / (ms * 1e-3)
     e2e_val = e2e_iters / (e2e_ms * 1e-3)
+    contact_steps = [t for t in time_steps if t["max_active"] > 0]
+    conv_contact = [t for t in contact_steps if t["converged"]]
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -443,8 +512,14 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded procedural scene, no paper meshes)",
         "config": {
             "workload": f"{sc.name}: {sc.n_tets} tets, {sc.n_verts} verts, h=1/30 s, dhat=1e-3 m",
+            "step": "one Algorithm 1 iteration (contact detection, projected-Hessian assembly, PCG, "
+                    "step bound + line search, AL update) of the time steps that follow the "
+                    "converged ones below",
             "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
-            "pcg_tol": args.pcg_tol, "newton_tol": args.newton_tol, "pcg_stall_window": args.pcg_stall,
+            "pcg_tol": args.pcg_tol, "pcg_max_iter": args.pcg_max, "newton_tol": args.newton_tol,
+            "pcg_stall_window": args.pcg_stall, "newton_cap": args.newton_max,
+            "spmv_window": args.spmv_window,
+            "sigma_rule": args.sigma_rule,
             "precond": args.precond, "precision": args.precision,
             "step_bound": args.step_mode, "broad_phase": args.broad_phase,
             "al_mode": args.al_mode, "pcg_tol_mode": args.pcg_tol_mode,
@@ -452,22 +527,38 @@ def run_ours(args, rank, world):
             "l2": "no flush: Hessian storage exceeds the 126 MB L2",
             "parallelism": f"replicas x{world}",
         },
-        "newton_iters_per_step": newton / max(args.steps, 1),
-        "newton_cap": args.newton_max,
-        "steps_converged": sum(int(t["converged"]) for t in timed),
-        "ms_per_newton_iter": round(ms / max(newton, 1), 2),
-        "pcg_iters_per_step": pcg_iters / max(args.steps, 1) / max(world, 1),
+        "time_steps": {
+            "ms_per_time_step": (round(statistics.mean(t["ms"] for t in conv_contact), 1)
+                                 if conv_contact and len(conv_contact) == len(contact_steps) else None),
+            "converged": f"{sum(t['converged'] for t in time_steps)}/{len(time_steps)}",
+            "newton_iters_per_contact_step": (round(statistics.mean(t["newton_iters"] for t in contact_steps), 1)
+                                              if contact_steps else None),
+            "note": "each time step from the initial state run to convergence (Alg. 1 test "
+                    "||e||/||e0|| <= newton_tol), timed with CUDA events; ms_per_time_step is the "
+                    "mean over the steps in contact, null unless all of them converged",
+            "steps": time_steps,
+        },
+        "alg1_iterations": {
+            "pcg_iters_per_iteration": round(pcg_iters / max(args.steps, 1) / max(world, 1), 1),
+            "max_active_pairs": max((t["n_active"] for t in timed), default=0),
+            "min_distance": min((t["dmin"] for t in timed), default=None),
+            "pcg_rel_residual_max": max((t["pcg_rel_residual"] for t in timed if t["pcg_iters"] > 0),
+                                        default=None),
+            "pcg_iters_per_solve": [t["pcg_iters"] for t in timed],
+            "time_steps_completed_in_run": state["time_steps_done"],
+            "phase_ms_per_iteration": {k: round(sum(t[k] for t in timed) / max(args.steps, 1), 2)
+                                       for k in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")},
+        },
         "pcg_only_iters_per_s": round(pcg_only, 1),
-        "max_active_pairs": max((t["max_active"] for t in timed), default=0),
-        "phase_ms_per_step": {k: round(sum(t[k] for t in timed) / max(args.steps, 1), 2)
-                              for k in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")},
         "e2e": {"value": round(e2e_val, 2), "unit": "PCG iter/s",
-                "h2d_bytes_per_step": 2 * 3 * nv * 8, "d2h_bytes_per_step": 2 * 3 * nv * 8},
+                "h2d_bytes_per_step": 3 * nv * 8, "d2h_bytes_per_step": 3 * nv * 8},
         "roofline": roofline_entry(args.precision, kname, achieved, peak, peak_kind, byts, spmv_ms,
-                                   k_n, nv, nnzL, nnzC, ncu_traffic(args.precision, args.scene)),
+                                   k_n, nv, nnzL, nnzC, ncu_traffic(args.precision, args.scene), fp64_peak),
+        "roofline_assembly": assembly_roofline(sc.n_tets, nv, nnzL, max_pairs, a_el_ms, a_tot_ms, a_n,
+                                               fp64_peak, peak, peak_kind),
+        "fp64_fma_tflops": round(fp64_peak, 4),
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "status": [t["status"] for t in timed],
     }
     if forms is not None:
         line["precision_forms"] = forms
@@ -518,11 +609,23 @@ def precision_forms(S, sc, dev, args):
     return out
 
 
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or None
+
+
 def cpu_baseline(args, nv_full, nnzL_full, nnzC_full, budget_s=15.0):
     """The FP64 oracle timed on this host's cores on a bounded sample: oracle
     assembly of a small chain-net scene and scipy CSR matvec of its Hessian,
     scaled by stored blocks to one PCG iteration (SpMV + 3 vector passes) of the
-    full workload."""
+    full workload. The matvec runs on one thread ("cores"); the host's core
+    count and CPU model are recorded beside it."""
     from oracle import system
     from paper_2407_00046_b300 import scenes
     t0 = time.perf_counter()
@@ -548,6 +651,7 @@ def cpu_baseline(args, nv_full, nnzL_full, nnzC_full, budget_s=15.0):
     t_vec = time.perf_counter() - tv
     t_iter = t_spmv * stored_full / stored_small + t_vec
     return {"value": round(1.0 / t_iter, 3), "unit": "PCG iter/s", "cores": 1, "kind": "oracle",
+            "host_cores": os.cpu_count(), "cpu_model": _cpu_model(),
             "sample": (f"oracle assembly ({sc.n_tets} tets, {t_asm:.2f} s) and scipy CSR matvec "
                        f"({stored_small} stored entries, {t_spmv * 1e3:.2f} ms) of a 3x3-ring "
                        f"chain net with one shell, scaled to {stored_full} stored entries "
@@ -590,15 +694,26 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10,
+                    help="timed bench steps: Algorithm 1 iterations (one pass of the hot path each)")
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--time-steps", type=int, default=3,
+                    help="time steps run to convergence and timed one by one before the bench steps "
+                         "(free fall, impact, first step in contact on the default workload)")
+    ap.add_argument("--sigma-rule", default="printed", choices=["printed", "capped"],
+                    help="Alg. 1 sigma update: the printed max(1.2 sigma, 100 sigma0), or the capped "
+                         "reading min(1.2 sigma, 100 sigma0)")
+    ap.add_argument("--pcg-max", type=int, default=30000, help="PCG iteration cap per solve")
+    ap.add_argument("--spmv-window", type=int, default=0,
+                    help="double-float SpMV: 0 = row gather with full column-side lists; W = windows "
+                         "of W rows with in-window transposes summed in shared memory")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scene", default="chain_net_shells")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS))
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
-    ap.add_argument("--newton-max", type=int, default=20,
-                    help="Newton iterations per time step (cap; the step reports convergence)")
+    ap.add_argument("--newton-max", type=int, default=400,
+                    help="Algorithm 1 iterations per time step (cap; the step reports convergence)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
     ap.add_argument("--precond", default="block-jacobi", choices=sorted(PRECONDS),

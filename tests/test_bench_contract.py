@@ -62,5 +62,6 @@ def test_default_run_is_one_gpu_a_few_steps():
         with pytest.raises(SystemExit):
             bench.main()
     d = captured["defaults"]
-    assert d["gpus"] == 1 and d["warmup"] >= 3 and 1 <= d["steps"] <= 5
+    assert d["gpus"] == 1 and d["warmup"] >= 3 and 1 <= d["steps"] <= 20
+    assert d["sigma_rule"] == "printed" and d["newton_max"] >= 200 and d["time_steps"] >= 2
     assert d["scene"] == "chain_net_shells" and d["precision"] == "df64"
