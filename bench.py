@@ -98,12 +98,16 @@ class Clocks:
         return out
 
 
-# FP64 operations per tet of k_elastic_hess<double> (projected Hessian: F,
+# FP64 instructions per tet of k_elastic_hess<double> (projected Hessian: F,
 # signed SVD by 3x3 Jacobi, the analytic eigensystem of the 9x9 dP/dF, the
-# 12x12 block and its slot scatter): ncu SASS counters of one launch on the
-# chain-net workload, 2 x DFMA + DADD + DMUL per tet
-# (profiles/k_elastic_hess_chain_net_shells.md).
-ELASTIC_HESS_FLOP_PER_TET = 2600.0
+# 12x12 block and its slot scatter), from the ncu SASS counters of one launch
+# on the 1,771,008-tet chain net (profiles/k_elastic_hess_chain_net_shells.md):
+# DADD 0.30 G, DMUL 0.84 G, DFMA 1.75 G. DADD and DMUL occupy the FP64 pipe
+# like DFMA, so the pipe's ceiling is the FMA issue rate (measured FP64 FMA
+# TFLOP/s / 2); flops count DFMA twice.
+ELASTIC_HESS_DADD_PER_TET = 0.30e9 / 1771008
+ELASTIC_HESS_DMUL_PER_TET = 0.84e9 / 1771008
+ELASTIC_HESS_DFMA_PER_TET = 1.75e9 / 1771008
 
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2, "fp32": 3}     # bal_precision values
@@ -188,13 +192,17 @@ def assembly_roofline(n_tets, nv, nnzL, n_pairs, elastic_ms, total_ms, n, fp64_p
     if n == 0:
         return None
     e_ms, t_ms = elastic_ms / n, total_ms / n
-    tf = ELASTIC_HESS_FLOP_PER_TET * n_tets / (e_ms * 1e-3) / 1e12
+    instr = (ELASTIC_HESS_DADD_PER_TET + ELASTIC_HESS_DMUL_PER_TET + ELASTIC_HESS_DFMA_PER_TET) * n_tets
+    flop = (ELASTIC_HESS_DADD_PER_TET + ELASTIC_HESS_DMUL_PER_TET + 2 * ELASTIC_HESS_DFMA_PER_TET) * n_tets
+    ti = instr / (e_ms * 1e-3) / 1e12
+    ipeak = fp64_peak / 2.0
     byts = assembly_bytes(n_tets, nv, nnzL, n_pairs)
     gbs = byts / (t_ms * 1e-3) / 1e9
-    return {"kernel": "k_elastic_hess<double>", "bound": "alu", "unit": "FP64 TFLOP/s",
-            "achieved": round(tf, 4), "peak": round(fp64_peak, 4), "frac": round(tf / fp64_peak, 4),
-            "peak_kind": "measured in this run (bal_fp64_fma_rate)", "ms_per_launch": round(e_ms, 4),
-            "flop_per_tet": ELASTIC_HESS_FLOP_PER_TET, "timed_assemblies": n,
+    return {"kernel": "k_elastic_hess<double>", "bound": "alu", "unit": "T FP64 instr/s",
+            "achieved": round(ti, 4), "peak": round(ipeak, 4), "frac": round(ti / ipeak, 4),
+            "peak_kind": "measured in this run (bal_fp64_fma_rate / 2: one FP64 pipe instruction per FMA)",
+            "flop_tflops": round(flop / (e_ms * 1e-3) / 1e12, 4), "ms_per_launch": round(e_ms, 4),
+            "fp64_instr_per_tet": round(instr / n_tets, 1), "timed_assemblies": n,
             "hbm": {"what": "whole assembly (element + contact stencils, duplicate merge, D^-1)",
                     "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(gbs / hbm_peak, 4), "peak_kind": peak_kind, "bytes": byts,
@@ -568,9 +576,10 @@ def run_ours(args, rank, world):
 
 
 def precision_forms(S, sc, dev, args):
-    """The solver forms -- three precisions with block-Jacobi, and in FP64 the
-    additive (App. A) and warm-start (Sec. 4.2.2) preconditioners -- on the
-    same system: the first Newton
+    """The solver forms -- three precisions with block-Jacobi (the FP32 +
+    FP64-refinement form with inner caps of 200, 1k, 3k and 10k FP32
+    iterations per pass), and in FP64 the additive (App. A) and warm-start
+    (Sec. 4.2.2) preconditioners -- on the same system: the first Newton
     system of the workload's first step (x = x_0, no contact; the 1 GPa links
     make it the stiff part, kappa ~ 1e8) -- solved from zero to the bench
     tolerance: iterations, time, FP64 relative residual and the relative
@@ -584,12 +593,14 @@ def precision_forms(S, sc, dev, args):
     S.assemble_hessian(x0, g)
     b = -g.view(-1)
     out, ref = {}, None
-    forms = [("fp64", "fp64", "block-jacobi"), ("df64", "df64", "block-jacobi"),
-             ("mixed", "mixed", "block-jacobi"), ("fp64_additive", "fp64", "additive"),
-             ("fp64_warm_start", "fp64", "warm-start")]
-    for name, prec, pc in forms:
+    # (name, precision, preconditioner, FP32 inner iteration cap of the mixed form)
+    forms = [("fp64", "fp64", "block-jacobi", 0), ("df64", "df64", "block-jacobi", 0),
+             ("mixed", "mixed", "block-jacobi", 200), ("mixed_inner1k", "mixed", "block-jacobi", 1000),
+             ("mixed_inner3k", "mixed", "block-jacobi", 3000), ("mixed_inner10k", "mixed", "block-jacobi", 10000),
+             ("fp64_additive", "fp64", "additive", 0), ("fp64_warm_start", "fp64", "warm-start", 0)]
+    for name, prec, pc, inner in forms:
         S.set_params(precision=PRECISIONS[prec], precond=PRECONDS[pc], pcg_stall_window=args.pcg_stall,
-                     mixed_inner_max=200, mixed_max_refine=40, mixed_inner_tol=1e-3,
+                     mixed_inner_max=max(inner, 1), mixed_max_refine=40, mixed_inner_tol=1e-3,
                      warm_tol=args.warm_tol, warm_max_iter=args.warm_iters)
         sol = torch.zeros_like(b)
         torch.cuda.synchronize()
@@ -703,7 +714,7 @@ def main():
     ap.add_argument("--sigma-rule", default="printed", choices=["printed", "capped"],
                     help="Alg. 1 sigma update: the printed max(1.2 sigma, 100 sigma0), or the capped "
                          "reading min(1.2 sigma, 100 sigma0)")
-    ap.add_argument("--pcg-max", type=int, default=30000, help="PCG iteration cap per solve")
+    ap.add_argument("--pcg-max", type=int, default=10000, help="PCG iteration cap per solve")
     ap.add_argument("--spmv-window", type=int, default=0,
                     help="double-float SpMV: 0 = row gather with full column-side lists; W = windows "
                          "of W rows with in-window transposes summed in shared memory")
@@ -729,7 +740,7 @@ def main():
                     help="friction coefficient chi of the fully-implicit friction (0 = frictionless)")
     ap.add_argument("--warm-tol", type=float, default=1e-2)
     ap.add_argument("--warm-iters", type=int, default=50)
-    ap.add_argument("--pcg-stall", type=int, default=5000,
+    ap.add_argument("--pcg-stall", type=int, default=2000,
                     help="PCG stagnation window (App. B uses 100; at 100 the block-Jacobi solves of "
                          "the 1 GPa net stop before their residual starts to fall)")
     ap.add_argument("--mode", default="step", choices=["step", "pcg", "adjoint", "precision-sweep"],

@@ -359,6 +359,105 @@ __global__ void __launch_bounds__(kDdThreads) k_dd_spmv(DDSys A, DDContact Cr, i
   }
 }
 
+// q = (D + L + L^T) p with one CTA per window of W consecutive rows (W a
+// multiple of 32; the slot order sorts rows only inside their window): p of
+// the window's rows is staged in shared memory; every row-side block L_ij
+// adds L_ij p_j to its row and, when row j lies in the same window (j < i <
+// window end, so j >= window start suffices), L_ij^T p_i to an FP64 shared
+// accumulator of row j; the transposes of blocks stored in later windows come
+// through the column-side list. Each row's own sum joins the accumulator, and
+// q is written in row order after a CTA barrier. The shared FP64 sums take
+// their terms in arrival order (atomics), so this layout is not
+// bit-reproducible (it is within FP64 rounding of the gather). Contact CTAs
+// as in k_dd_spmv.
+__device__ __forceinline__ dd3 ps_ld(const dd* ps, int r) { return dd3{ps[3 * r], ps[3 * r + 1], ps[3 * r + 2]}; }
+
+__global__ void __launch_bounds__(kDdThreads, 3) k_dd_spmv_win(DDSys A, DDContact Cr, int n_row_ctas, int W,
+                                                            const dd* __restrict__ p, dd* __restrict__ q,
+                                                            dd* __restrict__ qc, PcgScalars* P,
+                                                            double* partials) {
+  extern __shared__ double smw[];   // [W][3] FP64 sums, then [W][3] double-float p
+  pdl_enter();
+  if (P->done) return;
+  const int lane = threadIdx.x & 31;
+  dd pq{0.f, 0.f};
+  const int nc = gridDim.x - n_row_ctas;
+  const int K = nc > 0 ? (int)gridDim.x / nc : 1;
+  const int bj = blockIdx.x / K, br = blockIdx.x % K;
+  if (nc > 0 && br == K - 1 && bj < nc) {
+    pq = contact_rows<kContactLanes>(Cr, p, qc, bj, nc);
+  } else {
+    const int w = blockIdx.x - (nc > 0 ? min(nc, (int)(blockIdx.x + 1) / K) : 0);
+    const int w0 = w * W, w1 = min(A.nv, w0 + W), nw = w1 - w0;
+    double* acc = smw;
+    dd* ps = reinterpret_cast<dd*>(smw + 3 * W);
+    for (int r = threadIdx.x; r < nw; r += kDdThreads) {
+      const dd3 v = dd3_ld(p, w0 + r);
+      ps[3 * r] = v.x;
+      ps[3 * r + 1] = v.y;
+      ps[3 * r + 2] = v.z;
+      acc[3 * r] = acc[3 * r + 1] = acc[3 * r + 2] = 0.0;
+    }
+    __syncthreads();
+    const int s0 = w0 >> 5, s1 = (w1 + 31) >> 5;
+    for (int s = s0 + (threadIdx.x >> 5); s < s1; s += kDdWarps) {
+      const int slot = 32 * s + lane;
+      const int i = A.srow[slot];
+      const bool own = i >= 0;
+      const dd3 pi = own ? ps_ld(ps, i - w0) : dd3{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+      dd3 a = mv_sliced(A.D + slice_base(slot), pi);
+      const int lr = A.len[slot].x;
+      const int r0 = A.offR[s], r1 = A.offR[s + 1];
+#pragma unroll 2
+      for (int idx = r0 + lane; idx < r1; idx += 32) {
+        const bool real = idx - r0 < 32 * lr;
+        const int64_t vb = real ? 9 * (int64_t)(idx - lane) + lane : A.zero + 288 * (s % kZeroChunks) + lane;
+        const int j = A.Rcol[idx];
+        const dd* b = A.R + vb;
+        dd B[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) B[k] = b[32 * k];
+        const bool inw = j >= w0;
+        const dd3 pj = inw ? ps_ld(ps, j - w0) : dd3_ld(p, j);
+        a.x = dd_add(a.x, dd_fma(B[2], pj.z, dd_fma(B[1], pj.y, dd_mul(B[0], pj.x))));
+        a.y = dd_add(a.y, dd_fma(B[5], pj.z, dd_fma(B[4], pj.y, dd_mul(B[3], pj.x))));
+        a.z = dd_add(a.z, dd_fma(B[8], pj.z, dd_fma(B[7], pj.y, dd_mul(B[6], pj.x))));
+        if (real && inw) {   // L_ij^T p_i into row j's shared sum
+          double* aj = acc + 3 * (j - w0);
+          atomicAdd(aj, dd_to(dd_fma(B[6], pi.z, dd_fma(B[3], pi.y, dd_mul(B[0], pi.x)))));
+          atomicAdd(aj + 1, dd_to(dd_fma(B[7], pi.z, dd_fma(B[4], pi.y, dd_mul(B[1], pi.x)))));
+          atomicAdd(aj + 2, dd_to(dd_fma(B[8], pi.z, dd_fma(B[5], pi.y, dd_mul(B[2], pi.x)))));
+        }
+      }
+      const int t1 = A.offT[s + 1];
+#pragma unroll 2
+      for (int idx = A.offT[s] + lane; idx < t1; idx += 32)
+        dd3_acc(a, mtv_sliced(A.R + A.Tpos[idx], dd3_ld(p, A.Tsrc[idx])));
+      if (own) {
+        double* ai = acc + 3 * (i - w0);
+        atomicAdd(ai, dd_to(a.x));
+        atomicAdd(ai + 1, dd_to(a.y));
+        atomicAdd(ai + 2, dd_to(a.z));
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nw; r += kDdThreads) {
+      const dd3 qv{dd_from(acc[3 * r]), dd_from(acc[3 * r + 1]), dd_from(acc[3 * r + 2])};
+      dd3_st(q, w0 + r, qv);
+      pq = dd_add(pq, dd3_dot(ps_ld(ps, r), qv));
+    }
+  }
+  pq = dd_block_sum<kDdThreads>(pq);
+  if (threadIdx.x == 0) partials[blockIdx.x] = dd_to(pq);
+  if (dd_arrive_last(&P->counter)) {
+    const double tpq = dd_sum_partials<kDdThreads>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      set_alpha(P, tpq);
+      P->counter = 0;
+    }
+  }
+}
+
 // x += alpha p, r -= alpha q, z = D^{-1} r; rz, ||r||; convergence, stagnation, beta
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, const dd* __restrict__ p,
@@ -433,22 +532,32 @@ __global__ void k_dd_accumulate(int64_t n, double s, const dd* __restrict__ e, d
     x[i] += s * dd_to(e[i]);
 }
 
-// Sliced layout of the static lower blocks from the host CSR copy (once).
-bal_status build_sell(Scene& S) {
+// Sliced layout of the static lower blocks from the host CSR copy (once per
+// layout). win = 0: sorting windows of kSellWindow rows and full column-side
+// lists; win > 0: sorting windows of win rows (the windows of k_dd_spmv_win)
+// and column-side lists holding only the blocks stored in other windows.
+bal_status build_sell(Scene& S, int win) {
   const int nv = S.d.nv;
+  const int sw = win > 0 ? win : kSellWindow;
   const int64_t nL = S.d.nnzL;
   const int ns = (nv + 31) / 32;
   const std::vector<int32_t>& rp = S.row_ptr_h;
   const std::vector<int32_t>& col = S.col_h;
-  // column lists (ascending row) of the lower blocks
+  // column lists (ascending row) of the lower blocks; with windows, only the
+  // blocks whose row lies in another window than their column
+  auto listed = [&](int r, int c) { return win <= 0 || r / win != c / win; };
   std::vector<int32_t> cp(nv + 1, 0);
-  for (int64_t s = 0; s < nL; ++s) cp[col[s] + 1]++;
+  for (int r = 0; r < nv; ++r)
+    for (int32_t s = rp[r]; s < rp[r + 1]; ++s)
+      if (listed(r, col[s])) cp[col[s] + 1]++;
   for (int v = 0; v < nv; ++v) cp[v + 1] += cp[v];
-  std::vector<int32_t> cslot(nL > 0 ? nL : 1), crow(nL > 0 ? nL : 1);
+  const int64_t nList = cp[nv];
+  std::vector<int32_t> cslot(nList > 0 ? nList : 1), crow(nList > 0 ? nList : 1);
   {
     std::vector<int32_t> fill(cp.begin(), cp.end() - 1);
     for (int r = 0; r < nv; ++r)
       for (int32_t s = rp[r]; s < rp[r + 1]; ++s) {
+        if (!listed(r, col[s])) continue;
         const int32_t e = fill[col[s]]++;
         cslot[e] = s;
         crow[e] = r;
@@ -460,8 +569,8 @@ bal_status build_sell(Scene& S) {
   // padding (on a Kuhn-split lattice the lower-neighbour counts alternate
   // between 3 and 7 from one row to the next)
   std::vector<int32_t> srow((size_t)ns * 32, -1), slot_of(nv);
-  for (int w0 = 0; w0 < nv; w0 += kSellWindow) {
-    const int w1 = std::min(nv, w0 + kSellWindow);
+  for (int w0 = 0; w0 < nv; w0 += sw) {
+    const int w1 = std::min(nv, w0 + sw);
     std::vector<int32_t> rows(w1 - w0);
     for (int i = w0; i < w1; ++i) rows[i - w0] = i;
     std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t b) {
@@ -564,6 +673,7 @@ bal_status build_sell(Scene& S) {
   S.n_slices = ns;
   S.sell_zero = zero;
   S.sell_built = true;
+  S.sell_window = win;
   return BAL_OK;
 }
 
@@ -627,7 +737,7 @@ bal_status build_contact_rows(Scene& S, cudaStream_t st) {
 bal_status refresh_dd(Scene& S, bool* in_range, cudaStream_t st) {
   const int nv = S.d.nv;
   const int64_t nL = S.d.nnzL, nC = S.nnzC;
-  if (!S.sell_built) BAL_TRY(build_sell(S));
+  if (!S.sell_built || S.sell_window != S.prm.spmv_window) BAL_TRY(build_sell(S, S.prm.spmv_window));
   unsigned int* bad = reinterpret_cast<unsigned int*>(S.scal + 61);
   BAL_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
   k_dd_slices<<<grid_for(9 * (int64_t)nv), kThreads, 0, st>>>(nv, S.d.D, S.dd_D.as<dd>(), bad,
@@ -657,11 +767,12 @@ bal_status refresh_dd(Scene& S, bool* in_range, cudaStream_t st) {
 
 // launch with programmatic stream serialisation (the kernel calls pdl_enter)
 template <typename... K, typename... A>
-cudaError_t launch_pdl(void (*kernel)(K...), int grid, int block, cudaStream_t st, A&&... args) {
+cudaError_t launch_pdl_smem(void (*kernel)(K...), int grid, int block, size_t smem, cudaStream_t st,
+                            A&&... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -669,6 +780,10 @@ cudaError_t launch_pdl(void (*kernel)(K...), int grid, int block, cudaStream_t s
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), int grid, int block, cudaStream_t st, A&&... args) {
+  return launch_pdl_smem(kernel, grid, block, 0, st, std::forward<A>(args)...);
 }
 
 DDSys dd_sys(Scene& S) {
@@ -705,7 +820,7 @@ DDContact dd_contact(Scene& S) {
 bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it,
                     bal_solve_info* info, cudaStream_t st) {
   bool in_range = true;
-  if (!S.dd_valid) {
+  if (!S.dd_valid || S.sell_window != S.prm.spmv_window) {
     BAL_TRY(refresh_dd(S, &in_range, st));
     S.dd_valid = in_range;
   }
@@ -725,7 +840,16 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
   const DDContact Cr = dd_contact(S);
   dd* V = S.dd_vec.as<dd>();
   dd *ex = V, *er = V + n3, *ez = V + 2 * n3, *ep = V + 3 * n3, *eq = V + 4 * n3;
-  const int gs = std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
+  const int W = S.sell_window;   // 0: row-gather kernel; > 0: windowed kernel
+  const int gs = W > 0 ? (nv + W - 1) / W : std::min((S.n_slices + kDdWarps - 1) / kDdWarps, kMaxPartials / 2);
+  const size_t smem_w = W > 0 ? (size_t)W * 3 * (sizeof(double) + sizeof(dd)) : 0;
+  if (W > 0) {
+    if (gs > kMaxPartials / 2) {
+      set_error("df64 pcg: %d windows of %d rows exceed the %d partial sums", gs, W, kMaxPartials / 2);
+      return BAL_ERR_CAPACITY;
+    }
+    BAL_CUDA(cudaFuncSetAttribute(k_dd_spmv_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+  }
   const int gv = std::min((nv + kDdThreads - 1) / kDdThreads, kMaxPartials / 2);   // one vertex per thread
   // the update kernel takes two vertices per thread when that still leaves
   // at least 4 CTAs per SM
@@ -768,8 +892,12 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
         // one SpMV per chunk is timed: an event between two launches ends
         // their programmatic overlap
         if (k == 0) kt_before(S, 0, st);
-        BAL_CUDA(launch_pdl(k_dd_spmv, gs + gc, kDdThreads, st, A, Cr, gs, (const dd*)ep, eq, eqc, S.pcg,
-                            S.partials));
+        if (W > 0)
+          BAL_CUDA(launch_pdl_smem(k_dd_spmv_win, gs + gc, kDdThreads, smem_w, st, A, Cr, gs, W, (const dd*)ep,
+                                   eq, eqc, S.pcg, S.partials));
+        else
+          BAL_CUDA(launch_pdl(k_dd_spmv, gs + gc, kDdThreads, st, A, Cr, gs, (const dd*)ep, eq, eqc, S.pcg,
+                              S.partials));
         if (k == 0) {
           kt_after(S, 0, st);
           ++timed;

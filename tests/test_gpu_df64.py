@@ -239,3 +239,62 @@ def test_df64_trajectory_matches_oracle():
                                          precision=bal.PREC_DF64))
     m = system.make_model(sc)
     compare_trajectory(S, m, sc, 2, obal.Params(newton_tol=1e-8), T)
+
+
+def _textbook_iterates(H, b, n, iters):
+    Dinv = _diag_block_inverses(H, n)
+    prec = lambda r: np.einsum("nij,nj->ni", Dinv, r.reshape(n, 3)).ravel()  # noqa: E731
+    xr, r = np.zeros_like(b), b.copy()
+    z = prec(r)
+    p, rz = z.copy(), r @ z
+    for _ in range(iters):
+        q = H @ p
+        a = rz / (p @ q)
+        xr += a * p
+        r -= a * q
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return xr
+
+
+@pytest.mark.parametrize("case,window", [("stack", 32), ("stack", 512), ("stack", 1024),
+                                         ("shuffled", 64), ("shuffled", 4096), ("contact", 256)])
+def test_df64_windowed_spmv_iterates(case, window):
+    """The windowed SpMV layout (one CTA per window of rows, in-window transposes
+    summed in shared memory, the rest through the column-side list): three
+    iterates against textbook block-Jacobi CG on the oracle's Hessian, with
+    several windows and a ragged last one (5,488-vertex two-cube stack), a
+    shuffled vertex order (most transposes cross windows), and contact blocks.
+    The shared sums are FP64 in arrival order, so the bar is the df64 one."""
+    if case == "stack":
+        sc = scenes.cube_stack(n_cubes=2, n=13)
+        sigma, noise = 3.0, 2e-4
+    elif case == "shuffled":
+        sc, sigma, noise = _permuted(close_cubes(n=6), 7), 3.0, 1e-4
+    else:
+        sc, sigma, noise = close_cubes(n=6), 3.0, 1e-4
+    rng = np.random.default_rng(15)
+    x = sc.X + noise * rng.normal(size=sc.X.shape) * (sc.pinned == 0)[:, None]
+    S = bal.Scene(sc, bal.default_params(precision=bal.PREC_DF64, pcg_stall_window=0, spmv_window=window))
+    S.step_begin(T(sc.X), T(sc.V0))
+    S.set_al_state(sigma, sigma)
+    g = torch.empty(3 * sc.n_verts, dtype=torch.float64, device=DEV)
+    view = S.assemble_hessian(T(x), g)
+    if case == "contact":
+        assert view["nnz_C"] > 0
+    m, y, ps = oracle_state(sc, x, sigma)
+    H = system.hessian(m, x, y, ps, sigma).tocsr()
+    ref = _textbook_iterates(H, -g.cpu().numpy(), sc.n_verts, 3)
+    sol = torch.zeros_like(g)
+    info = S.pcg_solve(-g, sol, 1e-30, 3)
+    assert info["iters"] == 3 and info["precision_used"] == bal.PREC_DF64
+    assert np.abs(sol.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+    # a full solve reaches the FP64 residual
+    sol.zero_()
+    S.set_params(pcg_stall_window=1000)
+    info = S.pcg_solve(-g, sol, 1e-8, 20000)
+    bn = -g.cpu().numpy()
+    res = np.linalg.norm(bn - H @ sol.cpu().numpy()) / np.linalg.norm(bn)
+    assert info["converged"] == 1 and res <= 1.05e-8, (res, info)
