@@ -223,7 +223,7 @@ def run_pcg_only(args):
                                 broad_phase=BROAD_PHASES[args.broad_phase],
                                 mixed_inner_max=args.pcg_iters, mixed_max_refine=1, mixed_inner_tol=0.0,
                                 spmv_window=args.spmv_window)
-    S = bal.Scene(sc, params, pair_capacity=1 << 22)
+    S = bal.Scene(sc, params, pair_capacity=args.pair_capacity)
     x = torch.tensor(sc.X, dtype=torch.float64, device=dev)
     v = torch.tensor(sc.V0, dtype=torch.float64, device=dev)
     warm_steps = getattr(args, "pcg_warm_steps", 0)
@@ -292,8 +292,8 @@ def run_adjoint(args):
     x0 = torch.tensor(sc.X, dtype=torch.float64, device=dev).view(-1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    stats = []
-    xT, vT = simulate(S, x0, v0, E, args.adj_steps, require_converged=False, stats=stats)
+    stats, ckpts = [], []
+    xT, vT = simulate(S, x0, v0, E, args.adj_steps, require_converged=False, stats=stats, checkpoints=ckpts)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     m = mass[body]
@@ -302,14 +302,73 @@ def run_adjoint(args):
     J.backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    return {"mode": "adjoint", "scene": name, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
-            "steps": args.adj_steps, "precision_forward": args.precision,
-            "forward_ms_per_step": round(1e3 * (t1 - t0) / args.adj_steps, 1),
-            "backward_ms_per_step": round(1e3 * (t2 - t1) / args.adj_steps, 1),
-            "unconverged_forward_steps": stats[0]["unconverged_steps"] if stats else None,
-            "newton_cap": args.newton_max,
-            "loss": float(J), "grad_E_norm": float(E.grad.norm()), "grad_v0_norm": float(v0.grad.norm()),
-            "data": "synthetic (seeded procedural scene)"}
+    out = {"mode": "adjoint", "scene": name, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
+           "steps": args.adj_steps, "precision_forward": args.precision,
+           "forward_ms_per_step": round(1e3 * (t1 - t0) / args.adj_steps, 1),
+           "backward_ms_per_step": round(1e3 * (t2 - t1) / args.adj_steps, 1),
+           "unconverged_forward_steps": stats[0]["unconverged_steps"] if stats else None,
+           "newton_cap": args.newton_max, "newton_tol": args.newton_tol,
+           "loss": float(J), "grad_E_norm": float(E.grad.norm()), "grad_v0_norm": float(v0.grad.norm()),
+           "data": "synthetic (seeded procedural scene)"}
+    if args.adj_fd:
+        out["fd_check"] = adjoint_fd_check(S, x0, E, v0, mass, body, target, [c[3] for c in ckpts], args)
+    return out
+
+
+def adjoint_fd_check(S, x0, E, v0, mass, body, target, frozen, args, h=1e-6):
+    """Central finite differences of the same --adj-steps rollout, each step
+    re-solved with the AL state (sigma, A', mu) its differentiated run ended
+    with (the map the adjoint differentiates): along one random direction of
+    the per-tet E (relative step h) and one of the cube's initial velocity
+    (h m/s), and along --adj-fd-entries single entries of each with the
+    largest adjoint gradients. Reports adjoint and FD values and their
+    relative differences."""
+    import torch
+    rng = np.random.default_rng(17)
+    dev = x0.device
+    gE = E.grad.detach().clone()
+    gv = v0.grad.detach().clone()
+    E0 = E.detach().clone()
+
+    def rollout(Evals, vinit):
+        S.set_materials(Evals.cpu().numpy())
+        x, v = x0.clone(), vinit.clone()
+        S.set_params(freeze_al=1)
+        for f in frozen:
+            S.set_al_state(f["sigma"], f["sigma0"], f["ap_keys"], f["ap_mu"])
+            S.time_step(x, v, check=False)
+        S.set_params(freeze_al=0)
+        m = mass[body]
+        c = (m[:, None] * x.view(-1, 3)[body]).sum(0) / m.sum()
+        return float(((c - target) ** 2).sum())
+
+    checks = []
+
+    def fd(name, dE_rel, dv, adj):
+        jp = rollout(E0 * (1 + h * dE_rel), v0.detach() + h * dv)
+        jm = rollout(E0 * (1 - h * dE_rel), v0.detach() - h * dv)
+        val = (jp - jm) / (2 * h)
+        checks.append({"what": name, "adjoint": adj, "fd": val,
+                       "rel_diff": abs(adj - val) / max(abs(val), 1e-300)})
+
+    zE = torch.zeros_like(E0)
+    zv = torch.zeros_like(gv)
+    w = torch.tensor(rng.choice([-1.0, 1.0], size=E0.numel()), dtype=torch.float64, device=dev)
+    fd("E random direction (relative)", w, zv, float((gE * E0 * w).sum()))
+    u = torch.zeros_like(gv).view(-1, 3)
+    u[body] = torch.tensor(rng.normal(size=(body.numel(), 3)), dtype=torch.float64, device=dev)
+    u = u.view(-1)
+    fd("v0 random direction", zE, u, float((gv * u).sum()))
+    for i in torch.argsort((gE * E0).abs(), descending=True)[:args.adj_fd_entries].tolist():
+        e = zE.clone()
+        e[i] = 1.0
+        fd(f"E[{i}] (relative)", e, zv, float(gE[i] * E0[i]))
+    for i in torch.argsort(gv.abs(), descending=True)[:args.adj_fd_entries].tolist():
+        e = zv.clone()
+        e[i] = 1.0
+        fd(f"v0[{i}]", zE, e, float(gv[i]))
+    S.set_materials(E0.cpu().numpy())
+    return {"h": h, "checks": checks, "max_rel_diff": max(c["rel_diff"] for c in checks)}
 
 
 def run_precision_sweep(args):
@@ -575,6 +634,12 @@ def run_ours(args, rank, world):
     return line
 
 
+# The forms are compared on one system solved to the tolerance, so the
+# stagnation window must not end the 11k-iteration block-Jacobi solves of the
+# 1 GPa net early (the time-step bench uses a shorter one).
+FORMS_STALL_WINDOW = 20000
+
+
 def precision_forms(S, sc, dev, args):
     """The solver forms -- three precisions with block-Jacobi (the FP32 +
     FP64-refinement form with inner caps of 200, 1k, 3k and 10k FP32
@@ -599,7 +664,7 @@ def precision_forms(S, sc, dev, args):
              ("mixed_inner3k", "mixed", "block-jacobi", 3000), ("mixed_inner10k", "mixed", "block-jacobi", 10000),
              ("fp64_additive", "fp64", "additive", 0), ("fp64_warm_start", "fp64", "warm-start", 0)]
     for name, prec, pc, inner in forms:
-        S.set_params(precision=PRECISIONS[prec], precond=PRECONDS[pc], pcg_stall_window=args.pcg_stall,
+        S.set_params(precision=PRECISIONS[prec], precond=PRECONDS[pc], pcg_stall_window=FORMS_STALL_WINDOW,
                      mixed_inner_max=max(inner, 1), mixed_max_refine=40, mixed_inner_tol=1e-3,
                      warm_tol=args.warm_tol, warm_max_iter=args.warm_iters)
         sol = torch.zeros_like(b)
@@ -723,7 +788,7 @@ def main():
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS))
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
-    ap.add_argument("--newton-max", type=int, default=400,
+    ap.add_argument("--newton-max", type=int, default=800,
                     help="Algorithm 1 iterations per time step (cap; the step reports convergence)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
@@ -748,7 +813,13 @@ def main():
                          "forward + backward of --adj-steps steps through the autograd.Function; "
                          "precision-sweep: the same steps in FP64, df64 and FP32 + refinement")
     ap.add_argument("--adj-steps", type=int, default=20)
+    ap.add_argument("--adj-fd", action="store_true",
+                    help="--mode adjoint: central FD check of the gradient (AL state frozen per step)")
+    ap.add_argument("--adj-fd-entries", type=int, default=0,
+                    help="--adj-fd: also this many single E and v0 entries (largest gradients)")
     ap.add_argument("--pcg-iters", type=int, default=200)
+    ap.add_argument("--pair-capacity", type=int, default=1 << 22,
+                    help="--mode pcg: contact pair capacity of the scene (device memory for contact buffers)")
     ap.add_argument("--pcg-warm-steps", type=int, default=0,
                     help="--mode pcg: time steps taken before the assembly (a state in contact)")
     args = ap.parse_args()

@@ -61,8 +61,9 @@ typedef enum { BAL_PRECOND_BJ = 0, BAL_PRECOND_BJ_WARMSTART = 1, BAL_PRECOND_ADD
 
 /* Solver and schedule parameters. bal_default_params follows the paper: Newton
  * tolerance 1e-4 relative (Alg. 1 / Sec. 1 footnote), PCG 1e-4 relative with a
- * 100-iteration stagnation window (App. B), A' threshold 1e-2 dhat, sigma
- * growth 1.2 capped at 100 sigma0 (Alg. 1, Sec. 3.4), alpha_min 1e-9 (App. B). */
+ * 100-iteration stagnation window (App. B), A' threshold 1e-2 dhat, sigma <-
+ * max(1.2 sigma, 100 sigma0) while min d < 1e-2 dhat (Alg. 1, Sec. 3.4),
+ * alpha_min 1e-9 with rounds of 100 more PCG iterations below it (App. B). */
 typedef struct {
   int32_t precision;          /* bal_precision */
   int32_t precond;            /* bal_precond */
@@ -106,6 +107,8 @@ typedef struct {
                                  consecutive rows, transposed blocks of rows in the same
                                  window summed in shared memory (FP64), only the other
                                  windows' through the column-side list */
+  int32_t ls_extra_rounds;    /* App. B: rounds of ls_extra_pcg more PCG iterations tried while
+                                 the line search ends below ls_min_alpha (then failure) */
 } bal_params;
 
 /* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain

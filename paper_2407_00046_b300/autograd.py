@@ -11,7 +11,7 @@ from . import bal as _bal
 
 class _Simulate(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, E, v0, x0, scene, steps, adj_tol, require_converged=True, stats=None):
+    def forward(ctx, E, v0, x0, scene, steps, adj_tol, require_converged=True, stats=None, checkpoints=None):
         scene.set_materials(E.detach().cpu().double().numpy())
         x = x0.detach().clone().contiguous()
         v = v0.detach().clone().contiguous()
@@ -28,6 +28,8 @@ class _Simulate(torch.autograd.Function):
         ctx.scene, ctx.ckpt, ctx.nt, ctx.adj_tol = scene, ckpt, E.numel(), adj_tol
         if stats is not None:
             stats.append({"steps": steps, "unconverged_steps": ctx.unconverged})
+        if checkpoints is not None:
+            checkpoints.extend(ckpt)
         ctx.infos = []
         return x.clone(), v.clone()
 
@@ -41,13 +43,14 @@ class _Simulate(torch.autograd.Function):
         for xt, vt, xn, al in reversed(ctx.ckpt):
             gx, gv, info = S.adjoint_step(xt, vt, xn, al, gx, gv, dE, rel_tol=ctx.adj_tol)
             ctx.infos.append(info)
-        return dE, gv, gx, None, None, None, None, None
+        return dE, gv, gx, None, None, None, None, None, None
 
 
-def simulate(scene, x0, v0, E, steps, adj_tol=1e-12, require_converged=True, stats=None):
+def simulate(scene, x0, v0, E, steps, adj_tol=1e-12, require_converged=True, stats=None, checkpoints=None):
     """Differentiable T-step rollout: returns (x_T, v_T); gradients flow to
     E [n_tets], v0 and x0 [n_verts*3] (CUDA float64 tensors). With
     require_converged=False a step that ends at the Newton cap is kept and its
     adjoint is that of an approximate minimiser; stats (a list) receives the
-    number of such steps."""
-    return _Simulate.apply(E, v0, x0, scene, steps, adj_tol, require_converged, stats)
+    number of such steps; checkpoints (a list) receives the per-step
+    checkpoints (x_t, v_t, x_{t+1}, AL state)."""
+    return _Simulate.apply(E, v0, x0, scene, steps, adj_tol, require_converged, stats, checkpoints)

@@ -432,7 +432,7 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
 
   // line search (Alg. 1 line 8; Sec. 5.2 memory cap; App. B small steps)
   t0 = clk::now();
-  bool extra_done = false;
+  int extra_rounds = 0;
   for (;;) {
     auto tb = clk::now();
     BAL_TRY(find_candidates_motion(S, x, S.dir, S.ls_cand, S.ls_cand_alt, &S.n_ls_cand, st));
@@ -494,9 +494,10 @@ bal_status newton_iteration(Scene& S, double* x, bal_newton_info* info, cudaStre
       BAL_CUDA(cudaMemcpyAsync(x, S.xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
       break;
     }
-    if (!extra_done && S.prm.ls_extra_pcg > 0) {
-      // App. B: step below alpha_min -> more PCG iterations on the same system
-      extra_done = true;
+    if (extra_rounds < S.prm.ls_extra_rounds && S.prm.ls_extra_pcg > 0) {
+      // App. B: step below alpha_min -> more PCG iterations on the same system,
+      // continuing from the current direction, until the step grows
+      ++extra_rounds;
       BAL_TRY(pcg_solve(S, S.gtmp, S.dir, 0.0, S.prm.ls_extra_pcg, &si, st));
       I.pcg_iters += si.iters;
       continue;
@@ -578,7 +579,8 @@ static bool params_ok(const bal_params* p) {
       p->pcg_tol_mode < BAL_PCG_TOL_FIXED || p->pcg_tol_mode > BAL_PCG_TOL_COND_B ||
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
       !(p->friction >= 0) || !(p->friction_eps_v >= 0) ||
-      p->spmv_window < 0 || p->spmv_window > 4096 || (p->spmv_window % 32) != 0);
+      p->spmv_window < 0 || p->spmv_window > 4096 || (p->spmv_window % 32) != 0 ||
+      p->ls_extra_rounds < 0);
 }
 
 void bal_default_params(bal_params* p) {
@@ -615,6 +617,7 @@ void bal_default_params(bal_params* p) {
   p->friction = 0.0;
   p->friction_eps_v = 0.0;
   p->spmv_window = 0;
+  p->ls_extra_rounds = 10;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
