@@ -109,6 +109,10 @@ typedef struct {
                                  windows' through the column-side list */
   int32_t ls_extra_rounds;    /* App. B: rounds of ls_extra_pcg more PCG iterations tried while
                                  the line search ends below ls_min_alpha (then failure) */
+  double pcg_stall_forcing;   /* eta > 0: the stagnation window may end a solve only once
+                                 ||r|| <= eta ||r_0|| (otherwise the cap or the tolerance ends
+                                 it), so an inexact Newton direction reduces the linearised
+                                 residual at least by eta; 0 (default) = the window alone */
 } bal_params;
 
 /* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain

@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("freeze_al", C.c_int32), ("step_mode", C.c_int32), ("broad_phase", C.c_int32),
                 ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32),
                 ("friction", C.c_double), ("friction_eps_v", C.c_double),
-                ("spmv_window", C.c_int32), ("ls_extra_rounds", C.c_int32)]
+                ("spmv_window", C.c_int32), ("ls_extra_rounds", C.c_int32),
+                ("pcg_stall_forcing", C.c_double)]
 
 
 class SceneDesc(C.Structure):

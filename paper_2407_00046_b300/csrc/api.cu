@@ -580,7 +580,7 @@ static bool params_ok(const bal_params* p) {
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
       !(p->friction >= 0) || !(p->friction_eps_v >= 0) ||
       p->spmv_window < 0 || p->spmv_window > 4096 || (p->spmv_window % 32) != 0 ||
-      p->ls_extra_rounds < 0);
+      p->ls_extra_rounds < 0 || !(p->pcg_stall_forcing >= 0));
 }
 
 void bal_default_params(bal_params* p) {
@@ -618,6 +618,7 @@ void bal_default_params(bal_params* p) {
   p->friction_eps_v = 0.0;
   p->spmv_window = 0;
   p->ls_extra_rounds = 10;
+  p->pcg_stall_forcing = 0.0;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {

@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_dd_update(DDSys A, dd* __restrict__ x, c
       } else if (rn <= P->tol_abs) {
         P->done = 1;
         P->converged = 1;
-      } else if (it - P->best_it >= P->window) {
+      } else if (it - P->best_it >= P->window && rn <= P->stall_rel * P->r0norm) {
         P->done = 1;
         P->stagnated = 1;
       } else if (it >= P->max_it) {
@@ -870,6 +870,7 @@ bal_status pcg_df64(Scene& S, const double* b, double* x, double tol, int max_it
     PcgScalars init{};
     init.max_it = max_it - total;
     init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
+    init.stall_rel = S.prm.pcg_stall_forcing > 0 ? S.prm.pcg_stall_forcing : INFINITY;
     BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
     k_dd_init<kDdThreads><<<gv, kDdThreads, 0, st>>>(A, S.pcg_r, 1.0 / rn, ex, er, ez, S.pcg,
                                                             S.partials, tol * r0 / rn);

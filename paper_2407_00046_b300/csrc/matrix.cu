@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(Sys<T> A, T* __restrict__ x,
       } else if (rn <= P->tol_abs) {
         P->done = 1;
         P->converged = 1;
-      } else if (it - P->best_it >= P->window) {
+      } else if (it - P->best_it >= P->window && rn <= P->stall_rel * P->r0norm) {
         P->done = 1;
         P->stagnated = 1;
       } else if (it >= P->max_it) {
@@ -435,6 +435,7 @@ bal_status pcg_core(Scene& S, const Sys<T>& A, const T* b, const T* y0, T* x, T*
   PcgScalars init{};
   init.max_it = max_it;
   init.window = window > 0 ? window : (1 << 30);
+  init.stall_rel = S.prm.pcg_stall_forcing > 0 ? S.prm.pcg_stall_forcing : INFINITY;
   BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   k_pcg_init<T, NT><<<G, NT, 0, st>>>(A, b, y0, r, z, S.pcg, S.partials, tol);
   ::bal::note_launch();
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(NT) k_add_apply(Dev S, int ngroups, const doub
         else if (rn <= P->tol_abs) {
           P->done = 1;
           P->converged = 1;
-        } else if (it - P->best_it >= P->window) {
+        } else if (it - P->best_it >= P->window && rn <= P->stall_rel * P->r0norm) {
           P->done = 1;
           P->stagnated = 1;
         } else if (it >= P->max_it) {
@@ -789,8 +790,12 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     PcgScalars h;
     const int inner = std::min(S.prm.mixed_inner_max, max_it - total);
     const double itol = std::max(S.prm.mixed_inner_tol, 0.5 * tol * r0 / rn);
-    BAL_TRY(pcg_core<float>(S, A, S.b32, nullptr, S.x32, S.r32, S.z32, S.p32, S.q32, itol, inner,
-                            S.prm.pcg_stall_window, &h, st));
+    const bal_status ist = pcg_core<float>(S, A, S.b32, nullptr, S.x32, S.r32, S.z32, S.p32, S.q32, itol,
+                                           inner, S.prm.pcg_stall_window, &h, st);
+    // p^T H p <= 0 in FP32 (the FP32 copy of an ill-conditioned H loses
+    // definiteness in rounding) ends the inner solve: the iterate before it
+    // stands and the FP64 tests below decide; a non-finite residual is an error
+    if (ist != BAL_OK && h.done != 3) return ist;
     total += h.it;
     passes += 1;
     if (h.it == 0) break;
@@ -866,6 +871,7 @@ static bal_status pcg_additive(Scene& S, const double* b, double* x, double tol,
   PcgScalars init{};
   init.max_it = max_it;
   init.window = S.prm.pcg_stall_window > 0 ? S.prm.pcg_stall_window : (1 << 30);
+  init.stall_rel = S.prm.pcg_stall_forcing > 0 ? S.prm.pcg_stall_forcing : INFINITY;
   BAL_CUDA(cudaMemcpyAsync(S.pcg, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   k_pcg_init<double, NT><<<G, NT, 0, st>>>(A, b, S.pcg_q, S.pcg_r, S.pcg_z, S.pcg, S.partials, tol);
   ::bal::note_launch();

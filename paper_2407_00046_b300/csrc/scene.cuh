@@ -41,6 +41,7 @@ struct PcgScalars {
   uint32_t counter;   // last-block counter of the fused reductions
   uint32_t counter2;
   float alpha_hi, alpha_lo, beta_hi, beta_lo;   // alpha, beta as double-floats
+  double stall_rel;   // the stagnation window may end the solve only once ||r|| <= stall_rel ||r_0||
 };
 
 // Plain-old-data view of the scene's fixed device arrays, passed by value to kernels.
