@@ -790,7 +790,7 @@ def main():
                     help="Alg. 1 sigma update: the printed max(1.2 sigma, 100 sigma0), or the capped "
                          "reading min(1.2 sigma, 100 sigma0)")
     ap.add_argument("--pcg-max", type=int, default=10000, help="PCG iteration cap per solve")
-    ap.add_argument("--pcg-stall-forcing", type=float, default=0.0,
+    ap.add_argument("--pcg-stall-forcing", type=float, default=0.5,
                     help="eta > 0: the stagnation window may end a PCG solve only once ||r|| <= eta ||r0||")
     ap.add_argument("--spmv-window", type=int, default=0,
                     help="double-float SpMV: 0 = row gather with full column-side lists; W = windows "
