@@ -621,6 +621,7 @@ def run_ours(args, rank, world):
             "phase_ms_per_iteration": {k: round(sum(t[k] for t in timed) / max(args.steps, 1), 2)
                                        for k in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")},
         },
+        "max_active_pairs": max([t["max_active"] for t in time_steps] + [t["n_active"] for t in timed]),
         "pcg_only_iters_per_s": round(pcg_only, 1),
         "e2e": {"value": round(e2e_val, 2), "unit": "PCG iter/s",
                 "h2d_bytes_per_step": 3 * nv * 8, "d2h_bytes_per_step": 3 * nv * 8},

@@ -298,3 +298,25 @@ def test_df64_windowed_spmv_iterates(case, window):
     bn = -g.cpu().numpy()
     res = np.linalg.norm(bn - H @ sol.cpu().numpy()) / np.linalg.norm(bn)
     assert info["converged"] == 1 and res <= 1.05e-8, (res, info)
+
+
+@pytest.mark.parametrize("precision", [bal.PREC_DF64, bal.PREC_FP64])
+def test_stagnation_window_obeys_the_forcing_bound(multi_tile_case, precision):
+    """With a one-iteration stagnation window a solve stops at the first
+    iteration that does not improve sqrt(r^T z); with the forcing bound
+    eta = 0.5 it may stop that way only once ||r|| <= 0.5 ||r_0||."""
+    sc, S, x, b, H, m, y = multi_tile_case
+    bn = b.cpu().numpy()
+    out = {}
+    try:
+        for eta in (0.0, 0.5):
+            S.set_params(precision=precision, pcg_stall_window=1, pcg_stall_forcing=eta)
+            sol = torch.zeros_like(b)
+            info = S.pcg_solve(b, sol, 1e-12, 5000)
+            res = np.linalg.norm(bn - H @ sol.cpu().numpy()) / np.linalg.norm(bn)
+            out[eta] = (info, res)
+    finally:
+        S.set_params(precision=bal.PREC_FP64, pcg_stall_window=100, pcg_stall_forcing=0.0)
+    info, res = out[0.5]
+    assert info["converged"] == 1 or info["iters"] == 5000 or res <= 0.5 * 1.001, (info, res)
+    assert out[0.5][0]["iters"] >= out[0.0][0]["iters"]
