@@ -309,7 +309,7 @@ def run_adjoint(args):
            "backward_ms_per_step": round(1e3 * (t2 - t1) / args.adj_steps, 1),
            "unconverged_forward_steps": stats[0]["unconverged_steps"] if stats else None,
            "newton_cap": args.newton_max, "newton_tol": args.newton_tol,
-           "loss": float(J), "grad_E_norm": float(E.grad.norm()), "grad_v0_norm": float(v0.grad.norm()),
+           "loss": float(J.detach()), "grad_E_norm": float(E.grad.norm()), "grad_v0_norm": float(v0.grad.norm()),
            "data": "synthetic (seeded procedural scene)"}
     if args.adj_fd:
         out["fd_check"] = adjoint_fd_check(S, x0, E, v0, mass, body, target, [c[3] for c in ckpts], args)
@@ -346,9 +346,12 @@ def adjoint_fd_check(S, x0, E, v0, mass, body, target, frozen, args, h=1e-6):
     checks = []
 
     def fd(name, dE_rel, dv, adj):
+        t0 = time.perf_counter()
         jp = rollout(E0 * (1 + h * dE_rel), v0.detach() + h * dv)
         jm = rollout(E0 * (1 - h * dE_rel), v0.detach() - h * dv)
         val = (jp - jm) / (2 * h)
+        print(f"[bench] fd {name}: adjoint {adj:.9e} fd {val:.9e} ({time.perf_counter() - t0:.0f} s)",
+              file=sys.stderr, flush=True)
         checks.append({"what": name, "adjoint": adj, "fd": val,
                        "rel_diff": abs(adj - val) / max(abs(val), 1e-300)})
 
