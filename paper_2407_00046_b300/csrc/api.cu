@@ -885,7 +885,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
                  &S.sell_offR, &S.sell_offT, &S.sell_Rcol, &S.sell_Tpos, &S.sell_Tsrc, &S.sell_pos, &S.sell_len,
                  &S.sell_srow, &S.sell_slot, &S.fr_keys, &S.fr_beta, &S.fr_n, &S.fr_lam,
                  &S.dd_D, &S.dd_Dinv, &S.dd_R, &S.dd_C, &S.dd_vec, &S.cr_rows, &S.cr_ptr, &S.cr_ent,
-                 &S.cr_src, &S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_cnt, &S.cr_num,
+                 &S.cr_src, &S.cr_key, &S.cr_bucket, &S.cr_sorted, &S.cr_cnt, &S.cr_off, &S.cr_len, &S.cr_rpos,
                  &S.cr_of, &S.cr_q};
   for (Buf* b : bufs) buf_free(*b);
   delete sc;

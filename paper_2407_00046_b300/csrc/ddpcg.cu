@@ -25,7 +25,6 @@
 // adjacent rows, and their second read is served by L2. Contact blocks are
 // applied by extra CTAs of the same launch, eight lanes per contact row, into
 // a per-contact-row buffer that the update kernel adds to those rows.
-#include <cub/cub.cuh>
 #include <algorithm>
 #include <utility>
 
@@ -129,33 +128,46 @@ __global__ void k_to_dd(int64_t n, const double* __restrict__ a, dd* __restrict_
   }
 }
 
-// directed contact entries: e < nC applies C_e to row C_row[e]; e >= nC applies
-// C_{e-nC}^T to row C_col[e-nC]
+// directed contact entries keyed for the per-vertex bucket sort: entry 2c
+// applies C_c to row C_row[c], entry 2c + 1 applies C_c^T to row C_col[c];
+// key = row << 32 | entry, so record index = entry
 __global__ void k_crow_keys(const int32_t* __restrict__ crow, const int32_t* __restrict__ ccol, int nC,
-                            int32_t* __restrict__ key, int32_t* __restrict__ val) {
+                            uint64_t* __restrict__ key) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * nC; e += gridDim.x * blockDim.x) {
-    const bool tr = e >= nC;
-    const int c = tr ? e - nC : e;
-    key[e] = tr ? ccol[c] : crow[c];
-    val[e] = 2 * c + (tr ? 1 : 0);
+    const int c = e >> 1;
+    const int32_t r = (e & 1) ? ccol[c] : crow[c];
+    key[e] = ((uint64_t)(uint32_t)r << 32) | (uint32_t)e;
   }
 }
+// flag[v] = 1 where vertex v has contact entries
+__global__ void k_crow_flag(const int32_t* __restrict__ len, int nv, int32_t* __restrict__ flag) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+    flag[v] = len[v] > 0 ? 1 : 0;
+}
+// contact row r = rpos[v] of each vertex with entries: rows[r] = v, ptr[r] =
+// off[v], crow_of[v] = r (-1 for the others); ptr[number of rows] = n2
+__global__ void k_crow_rows(const int32_t* __restrict__ len, const int32_t* __restrict__ off,
+                            const int32_t* __restrict__ rpos, int nv, int n2, int32_t* __restrict__ rows,
+                            int32_t* __restrict__ ptr, int32_t* __restrict__ crow_of) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    if (len[v] > 0) {
+      const int r = rpos[v];
+      rows[r] = v;
+      ptr[r] = off[v];
+      crow_of[v] = r;
+    } else {
+      crow_of[v] = -1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ptr[rpos[nv]] = n2;
+}
+// source vertex of each ordered entry
 __global__ void k_crow_src(const int32_t* __restrict__ ent, const int32_t* __restrict__ crow,
-                           const int32_t* __restrict__ ccol, int n2, const int32_t* __restrict__ nrows,
-                           int32_t* __restrict__ src, int32_t* __restrict__ ptr) {
+                           const int32_t* __restrict__ ccol, int n2, int32_t* __restrict__ src) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += gridDim.x * blockDim.x) {
     const int c = ent[e] >> 1;
     src[e] = (ent[e] & 1) ? crow[c] : ccol[c];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ptr[*nrows] = n2;
-}
-
-// crow_of[rows[c]] = c for the *nrows unique contact rows
-__global__ void k_crow_of(const int32_t* __restrict__ rows, int n2, const int32_t* __restrict__ nrows,
-                          int32_t* __restrict__ crow_of) {
-  const int n = *nrows;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n && c < n2; c += gridDim.x * blockDim.x)
-    crow_of[rows[c]] = c;
 }
 
 // Programmatic dependent launch: a PCG-loop kernel lets the next one in the
@@ -677,56 +689,45 @@ bal_status build_sell(Scene& S, int win) {
   return BAL_OK;
 }
 
-// contact rows of the current C: unique rows of C and C^T with their entries
+// contact rows of the current C: the vertices touched by C or C^T, each with
+// its entries ordered by entry index (a counting sort by vertex, then a rank
+// sort inside each vertex's bucket: deterministic, no library sort)
 bal_status build_contact_rows(Scene& S, cudaStream_t st) {
-  const int nC = (int)S.nnzC, n2 = 2 * nC;
+  const int nC = (int)S.nnzC, n2 = 2 * nC, nv = S.d.nv;
   S.n_crows = 0;
   if (nC == 0) return BAL_OK;
-  for (Buf* b : {&S.cr_key, &S.cr_key_alt, &S.cr_val, &S.cr_val_alt, &S.cr_src, &S.cr_rows, &S.cr_cnt,
-                 &S.cr_ent})
+  BAL_TRY(buf_reserve(S.cr_key, sizeof(uint64_t) * n2));
+  for (Buf* b : {&S.cr_bucket, &S.cr_ent, &S.cr_src, &S.cr_rows})
     BAL_TRY(buf_reserve(*b, sizeof(int32_t) * n2));
   BAL_TRY(buf_reserve(S.cr_ptr, sizeof(int32_t) * (n2 + 1)));
-  BAL_TRY(buf_reserve(S.cr_num, sizeof(int32_t)));
-  k_crow_keys<<<grid_for(n2), kThreads, 0, st>>>(S.C_row.as<int32_t>(), S.C_col.as<int32_t>(), nC,
-                                                 S.cr_key.as<int32_t>(), S.cr_val.as<int32_t>());
+  for (Buf* b : {&S.cr_cnt, &S.cr_off, &S.cr_len, &S.cr_rpos})
+    BAL_TRY(buf_reserve(*b, sizeof(int32_t) * ((size_t)nv + 1)));
+  const int32_t* crow = S.C_row.as<int32_t>();
+  const int32_t* ccol = S.C_col.as<int32_t>();
+  k_crow_keys<<<grid_for(n2), kThreads, 0, st>>>(crow, ccol, nC, S.cr_key.as<uint64_t>());
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
-  cub::DoubleBuffer<int32_t> dk(S.cr_key.as<int32_t>(), S.cr_key_alt.as<int32_t>());
-  cub::DoubleBuffer<int32_t> dv(S.cr_val.as<int32_t>(), S.cr_val_alt.as<int32_t>());
-  int bits = 1;
-  while (bits < 31 && (1 << bits) <= S.d.nv) ++bits;
-  size_t tmp = 0;
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, n2, 0, bits, st));
-  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceRadixSort::SortPairs(S.cub_tmp.p, tmp, dk, dv, n2, 0, bits, st));
-  int32_t* keys = dk.Current();
-  int32_t* num = S.cr_num.as<int32_t>();
-  BAL_CUDA(cudaMemsetAsync(S.cr_cnt.p, 0, sizeof(int32_t) * n2, st));
-  tmp = 0;
-  BAL_CUDA(cub::DeviceRunLengthEncode::Encode(nullptr, tmp, keys, S.cr_rows.as<int32_t>(),
-                                              S.cr_cnt.as<int32_t>(), num, n2, st));
-  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceRunLengthEncode::Encode(S.cub_tmp.p, tmp, keys, S.cr_rows.as<int32_t>(),
-                                              S.cr_cnt.as<int32_t>(), num, n2, st));
-  tmp = 0;
-  BAL_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, S.cr_cnt.as<int32_t>(), S.cr_ptr.as<int32_t>(), n2, st));
-  BAL_TRY(buf_reserve(S.cub_tmp, tmp));
-  BAL_CUDA(cub::DeviceScan::ExclusiveSum(S.cub_tmp.p, tmp, S.cr_cnt.as<int32_t>(), S.cr_ptr.as<int32_t>(), n2, st));
-  BAL_CUDA(cudaMemcpyAsync(S.cr_ent.p, dv.Current(), sizeof(int32_t) * n2, cudaMemcpyDeviceToDevice, st));
-  k_crow_src<<<grid_for(n2), kThreads, 0, st>>>(S.cr_ent.as<int32_t>(), S.C_row.as<int32_t>(),
-                                                S.C_col.as<int32_t>(), n2, num, S.cr_src.as<int32_t>(),
-                                                S.cr_ptr.as<int32_t>());
+  int32_t* off = S.cr_off.as<int32_t>();
+  int32_t* len = S.cr_len.as<int32_t>();
+  int32_t* rpos = S.cr_rpos.as<int32_t>();
+  BAL_TRY(rows_bucket(S, S.cr_key.as<uint64_t>(), n2, nv, S.cr_cnt.as<int32_t>(), off,
+                      S.cr_bucket.as<int32_t>(), S.cr_ent.as<int32_t>(), len, st));
+  k_crow_flag<<<grid_for(nv), kThreads, 0, st>>>(len, nv, S.cr_cnt.as<int32_t>());
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
+  BAL_TRY(scan_i32(S, S.cr_cnt.as<int32_t>(), rpos, nv, st));
   // vertex -> contact row, and room for the contact part of H p per contact row
-  BAL_TRY(buf_reserve(S.cr_of, sizeof(int32_t) * (size_t)S.d.nv));
+  BAL_TRY(buf_reserve(S.cr_of, sizeof(int32_t) * (size_t)nv));
   BAL_TRY(buf_reserve(S.cr_q, sizeof(dd) * 3 * (size_t)n2));
-  BAL_CUDA(cudaMemsetAsync(S.cr_of.p, 0xff, sizeof(int32_t) * (size_t)S.d.nv, st));   // -1
-  k_crow_of<<<grid_for(n2), kThreads, 0, st>>>(S.cr_rows.as<int32_t>(), n2, num, S.cr_of.as<int32_t>());
+  k_crow_rows<<<grid_for(nv), kThreads, 0, st>>>(len, off, rpos, nv, n2, S.cr_rows.as<int32_t>(),
+                                                 S.cr_ptr.as<int32_t>(), S.cr_of.as<int32_t>());
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  k_crow_src<<<grid_for(n2), kThreads, 0, st>>>(S.cr_ent.as<int32_t>(), crow, ccol, n2, S.cr_src.as<int32_t>());
   ::bal::note_launch();
   BAL_LAUNCH_CHECK();
   int32_t n = 0;
-  BAL_CUDA(cudaMemcpyAsync(&n, num, sizeof(n), cudaMemcpyDeviceToHost, st));
+  BAL_CUDA(cudaMemcpyAsync(&n, rpos + nv, sizeof(n), cudaMemcpyDeviceToHost, st));
   BAL_CUDA(cudaStreamSynchronize(st));
   S.n_crows = n;
   return BAL_OK;

@@ -108,7 +108,10 @@ struct Scene {
   // contact rows (per assembly): unique rows touched by C or C^T, their entries
   // (2c + transposed) and source vertices in CSR form
   int32_t n_crows = 0;
-  Buf cr_rows, cr_ptr, cr_ent, cr_src, cr_key, cr_key_alt, cr_val, cr_val_alt, cr_cnt, cr_num;
+  Buf cr_rows, cr_ptr, cr_ent, cr_src;
+  // their build (rows_bucket): keys vertex << 32 | entry, bucket scratch,
+  // ordered entry indices, per-vertex counts / offsets / entries, row positions
+  Buf cr_key, cr_bucket, cr_sorted, cr_cnt, cr_off, cr_len, cr_rpos;
   Buf cr_of, cr_q;               // vertex -> contact row (-1: none); contact part of H p per contact row
   bool assembled = false;
   bool project = true;           // PSD projection of stencil Hessians (false: adjoint)
@@ -253,6 +256,8 @@ bal_status lbvh_candidates(Scene& S, const double* x, const double* dir, double 
 // ---- matrix.cu -----------------------------------------------------------------
 bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st);
 bal_status scan_i32(Scene& S, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+bal_status rows_bucket(Scene& S, const uint64_t* keys, int64_t n, int nv, int32_t* cnt, int32_t* off,
+                       int32_t* bucket, int32_t* sorted, int32_t* ucnt, cudaStream_t st);
 bal_status launch_dinv(Scene& S, cudaStream_t st);
 bal_status spmv(Scene& S, const double* v, double* y, cudaStream_t st);
 bal_status spmv32(Scene& S, const float* v, float* y, cudaStream_t st);

@@ -277,6 +277,29 @@ bal_status scan_i32(Scene& S, const int32_t* in, int32_t* out, int64_t n, cudaSt
   return BAL_OK;
 }
 
+// Counting sort of n records (keys[i] = row << 32 | col, ~0 = dropped) into
+// per-row buckets, each ordered by (col, record index): off[0..nv] are the
+// bucket offsets, sorted[off[r] .. off[r+1]) the record indices of row r and
+// ucnt[r] its number of distinct columns. cnt ([nv + 1]) and bucket ([n]) are
+// scratch. No host synchronisation.
+bal_status rows_bucket(Scene& S, const uint64_t* keys, int64_t n, int nv, int32_t* cnt, int32_t* off,
+                       int32_t* bucket, int32_t* sorted, int32_t* ucnt, cudaStream_t st) {
+  const size_t nrow = (size_t)nv + 1;
+  BAL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nrow, st));
+  k_cm_count<<<grid_for(n), kThreads, 0, st>>>(keys, n, cnt);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(scan_i32(S, cnt, off, nv, st));
+  BAL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nrow, st));   // reused as the fill counters
+  k_cm_scatter<<<grid_for(n), kThreads, 0, st>>>(keys, n, off, cnt, bucket);
+  ::bal::note_launch();
+  const int row_blocks = grid_for((int64_t)nv * 32, kThreads, kNumSM * 16);
+  k_cm_order<<<row_blocks, kThreads, 0, st>>>(keys, off, nv, bucket, sorted, ucnt);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  return BAL_OK;
+}
+
 // Merge the n_emit emitted contact blocks (S.emit_keys: row << 32 | col, ~0 =
 // dropped; S.emit_vals: [n_emit][9]) into C (S.C_row, S.C_col, S.C_val, S.nnzC),
 // sorted by (row, col).
@@ -290,21 +313,10 @@ bal_status contact_blocks_reduce(Scene& S, int64_t n_emit, cudaStream_t st) {
   BAL_TRY(buf_reserve(S.cm_bucket, sizeof(int32_t) * n_emit));
   BAL_TRY(buf_reserve(S.cm_sorted, sizeof(int32_t) * n_emit));
   const uint64_t* keys = S.emit_keys.as<uint64_t>();
-  int32_t* cnt = S.cm_cnt.as<int32_t>();
   int32_t* off = S.cm_off.as<int32_t>();
-  BAL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nrow, st));
-  k_cm_count<<<grid_for(n_emit), kThreads, 0, st>>>(keys, n_emit, cnt);
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
-  BAL_TRY(scan_i32(S, cnt, off, nv, st));
-  BAL_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nrow, st));   // reused as the fill counters
-  k_cm_scatter<<<grid_for(n_emit), kThreads, 0, st>>>(keys, n_emit, off, cnt, S.cm_bucket.as<int32_t>());
-  ::bal::note_launch();
+  BAL_TRY(rows_bucket(S, keys, n_emit, nv, S.cm_cnt.as<int32_t>(), off, S.cm_bucket.as<int32_t>(),
+                      S.cm_sorted.as<int32_t>(), S.cm_ucnt.as<int32_t>(), st));
   const int row_blocks = grid_for((int64_t)nv * 32, kThreads, kNumSM * 16);
-  k_cm_order<<<row_blocks, kThreads, 0, st>>>(keys, off, nv, S.cm_bucket.as<int32_t>(),
-                                              S.cm_sorted.as<int32_t>(), S.cm_ucnt.as<int32_t>());
-  ::bal::note_launch();
-  BAL_LAUNCH_CHECK();
   int32_t* uoff = S.cm_uoff.as<int32_t>();
   BAL_TRY(scan_i32(S, S.cm_ucnt.as<int32_t>(), uoff, nv, st));
   int32_t nC = 0;
