@@ -390,8 +390,8 @@ def run_precision_sweep(args):
     for prec in ("fp64", "df64", "mixed"):
         a = argparse.Namespace(**vars(args))
         a.precision = prec
-        S = bal.Scene(sc, _scene_params(a, bal, mixed_inner_max=200, mixed_max_refine=40,
-                                        mixed_inner_tol=1e-3), pair_capacity=1 << 22)
+        S = bal.Scene(sc, _scene_params(a, bal, mixed_inner_max=3000, mixed_max_refine=60,
+                                        mixed_inner_tol=1e-2), pair_capacity=1 << 22)
         x = torch.tensor(sc.X, dtype=torch.float64, device=dev).contiguous()
         v = torch.tensor(sc.V0, dtype=torch.float64, device=dev).contiguous()
         infos = []
@@ -647,17 +647,21 @@ def run_ours(args, rank, world):
 # stagnation window must not end the 11k-iteration block-Jacobi solves of the
 # 1 GPa net early (the time-step bench uses a shorter one).
 FORMS_STALL_WINDOW = 20000
+# FP32 + refinement restarts CG every pass and its FP32 operator differs from
+# H by ~kappa eps_32 on the stiff modes, so it takes several times the FP64
+# form's iterations on the net.
+FORMS_MAX_ITER_MIXED = 100000
 
 
 def precision_forms(S, sc, dev, args):
     """The solver forms -- three precisions with block-Jacobi (the FP32 +
-    FP64-refinement form with inner caps of 200, 1k, 3k and 10k FP32
-    iterations per pass), and in FP64 the additive (App. A) and warm-start
-    (Sec. 4.2.2) preconditioners -- on the same system: the first Newton
-    system of the workload's first step (x = x_0, no contact; the 1 GPa links
-    make it the stiff part, kappa ~ 1e8) -- solved from zero to the bench
-    tolerance: iterations, time, FP64 relative residual and the relative
-    difference of the solution to the FP64 one."""
+    FP64-refinement form with the FP32 operator in difference form, inner caps
+    of 3k and 10k FP32 iterations per pass, and in the plain form), and in FP64
+    the additive (App. A) and warm-start (Sec. 4.2.2) preconditioners -- on the
+    same system: the first Newton system of the workload's first step (x =
+    x_0, no contact; the 1 GPa links make it the stiff part, kappa ~ 1e8) --
+    solved from zero to the bench tolerance: iterations, time, FP64 relative
+    residual and the relative difference of the solution to the FP64 one."""
     import torch
     from paper_2407_00046_b300 import bal
     keep = S.get_params()
@@ -668,20 +672,22 @@ def precision_forms(S, sc, dev, args):
     S.assemble_hessian(x0, g)
     b = -g.view(-1)
     out, ref = {}, None
-    # (name, precision, preconditioner, FP32 inner iteration cap of the mixed form)
-    forms = [("fp64", "fp64", "block-jacobi", 0), ("df64", "df64", "block-jacobi", 0),
-             ("mixed", "mixed", "block-jacobi", 200), ("mixed_inner1k", "mixed", "block-jacobi", 1000),
-             ("mixed_inner3k", "mixed", "block-jacobi", 3000), ("mixed_inner10k", "mixed", "block-jacobi", 10000),
-             ("fp64_additive", "fp64", "additive", 0), ("fp64_warm_start", "fp64", "warm-start", 0)]
-    for name, prec, pc, inner in forms:
+    # (name, precision, preconditioner, FP32 inner iteration cap, FP32 operator form)
+    diff, plain = bal.MIXED_OP_DIFFERENCE, bal.MIXED_OP_PLAIN
+    forms = [("fp64", "fp64", "block-jacobi", 0, diff), ("df64", "df64", "block-jacobi", 0, diff),
+             ("mixed", "mixed", "block-jacobi", 3000, diff),
+             ("mixed_inner10k", "mixed", "block-jacobi", 10000, diff),
+             ("mixed_plain", "mixed", "block-jacobi", 3000, plain),
+             ("fp64_additive", "fp64", "additive", 0, diff), ("fp64_warm_start", "fp64", "warm-start", 0, diff)]
+    for name, prec, pc, inner, op in forms:
         S.set_params(precision=PRECISIONS[prec], precond=PRECONDS[pc], pcg_stall_window=FORMS_STALL_WINDOW,
-                     mixed_inner_max=max(inner, 1), mixed_max_refine=40, mixed_inner_tol=1e-3,
-                     warm_tol=args.warm_tol, warm_max_iter=args.warm_iters)
+                     mixed_inner_max=max(inner, 1), mixed_max_refine=60, mixed_inner_tol=1e-2,
+                     mixed_operator=op, warm_tol=args.warm_tol, warm_max_iter=args.warm_iters)
         sol = torch.zeros_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            info = S.pcg_solve(b, sol, args.pcg_tol, 30000)
+            info = S.pcg_solve(b, sol, args.pcg_tol, FORMS_MAX_ITER_MIXED if prec == "mixed" else 30000)
         except bal.BalError as e:          # reported, not fatal to the line
             out[name] = {"error": str(e)}
             continue
@@ -689,14 +695,30 @@ def precision_forms(S, sc, dev, args):
         sec = time.perf_counter() - t0
         if ref is None:
             ref = sol.clone()
-        diff = float((sol - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
+        diff_rel = float((sol - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
         out[name] = {"iters": info["iters"], "seconds": round(sec, 3), "converged": info["converged"],
                      "rel_residual": info["rel_residual"], "refine_passes": info["refine_passes"],
-                     "max_rel_diff_vs_fp64": diff, "precision_used": info["precision_used"],
+                     "max_rel_diff_vs_fp64": diff_rel, "precision_used": info["precision_used"],
                      "warm_iters": info["warm_iters"]}
+        if prec == "mixed":
+            out[name]["fp32_operator"] = "difference" if op == diff else "plain"
     S.set_params(keep)
     out["system"] = "first Newton system of step 1 (x = x_0), rhs = -gradient, x from 0"
     return out
+
+
+def run_forms(args):
+    """--mode forms: only the solver-form comparison (precision_forms) on the
+    workload's first Newton system."""
+    import torch
+    from paper_2407_00046_b300 import bal, build, scenes
+    build.build(force=False, verbose=False)
+    dev = torch.device("cuda", 0)
+    sc = scenes.scene_by_name(args.scene)
+    S = bal.Scene(sc, _scene_params(args, bal), pair_capacity=1 << 22)
+    out = precision_forms(S, sc, dev, args)
+    return {"mode": "forms", "scene": args.scene, "n_tets": sc.n_tets, "n_verts": sc.n_verts,
+            "pcg_tol": args.pcg_tol, "forms": out, "data": "synthetic (seeded procedural scene)"}
 
 
 def _cpu_model():
@@ -824,10 +846,11 @@ def main():
     ap.add_argument("--pcg-stall", type=int, default=2000,
                     help="PCG stagnation window (App. B uses 100; at 100 the block-Jacobi solves of "
                          "the 1 GPa net stop before their residual starts to fall)")
-    ap.add_argument("--mode", default="step", choices=["step", "pcg", "adjoint", "precision-sweep"],
+    ap.add_argument("--mode", default="step", choices=["step", "pcg", "adjoint", "precision-sweep", "forms"],
                     help="pcg: assemble once and time fixed-length PCG solves (profiling); adjoint: "
                          "forward + backward of --adj-steps steps through the autograd.Function; "
-                         "precision-sweep: the same steps in FP64, df64 and FP32 + refinement")
+                         "precision-sweep: the same steps in FP64, df64 and FP32 + refinement; forms: "
+                         "only the solver-form comparison on the first Newton system")
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--adj-fd", action="store_true",
                     help="--mode adjoint: central FD check of the gradient (AL state frozen per step)")
@@ -842,8 +865,9 @@ def main():
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if args.mode in ("pcg", "adjoint", "precision-sweep"):
-        run = {"pcg": run_pcg_only, "adjoint": run_adjoint, "precision-sweep": run_precision_sweep}
+    if args.mode in ("pcg", "adjoint", "precision-sweep", "forms"):
+        run = {"pcg": run_pcg_only, "adjoint": run_adjoint, "precision-sweep": run_precision_sweep,
+               "forms": run_forms}
         if rank == 0:
             print(json.dumps(run[args.mode](args)), flush=True)
         return

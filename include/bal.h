@@ -44,7 +44,11 @@ typedef enum {
 } bal_status;
 
 /* FP64: every PCG operation in FP64. MIXED: FP32 inner PCG with FP64 iterative
- * refinement. DF64: PCG recurrences in double-float arithmetic (pairs of FP32,
+ * refinement -- each pass solves H e = r / ||r|| in FP32 (mixed_inner_tol,
+ * mixed_inner_max) and is kept if it lowers the FP64 quadratic model
+ * x^T H x / 2 - b^T x (its change -d.(r + r_new)/2 formed from the correction d
+ * and the two FP64 residuals) or the FP64 residual; a pass that lowers neither
+ * is rolled back and ends the solve. DF64: PCG recurrences in double-float arithmetic (pairs of FP32,
  * ~47-bit significand) with FP64 residuals deciding convergence; falls back to
  * FP64 for a matrix with an entry beyond 1e36. */
 /* FP32: the single-precision path (the paper's single-precision version,
@@ -53,6 +57,15 @@ typedef enum {
  * refinement). Contact distances, barrier derivatives, the gradient, the
  * residual norms and the line-search energies stay FP64. */
 typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2, BAL_PREC_FP32 = 3 } bal_precision;
+/* The FP32 operator of the FP32 + FP64-refinement solves (BAL_PREC_MIXED,
+ * BAL_PREC_FP32; no counterpart in the paper, whose solver is FP64).
+ * DIFFERENCE: (H v)_i = G_i v_i + sum_j B_ij (v_j - v_i), with
+ * G_i = D_i + the sum of row i's off-diagonal blocks summed in FP64 before its
+ * one rounding (m_i/h^2 I wherever every block of the row is translation
+ * invariant) -- the form stays exactly translation invariant in FP32, so
+ * rounding the blocks of a stiff body barely moves its near-rigid modes.
+ * PLAIN: D_i v_i + sum_j B_ij v_j with every block rounded to FP32. */
+typedef enum { BAL_MIXED_OP_DIFFERENCE = 0, BAL_MIXED_OP_PLAIN = 1 } bal_mixed_operator;
 /* BJ: block-Jacobi. BJ_WARMSTART: block-Jacobi after the stiffness-grouped
  * warm start (Sec. 4.2.2). ADDITIVE: the two-level additive preconditioner the
  * paper compares against (App. A): 3x3 diagonal-block inverses plus exact
@@ -113,6 +126,7 @@ typedef struct {
                                  ||r|| <= eta ||r_0|| (otherwise the cap or the tolerance ends
                                  it), so an inexact Newton direction reduces the linearised
                                  residual at least by eta; 0 (default) = the window alone */
+  int32_t mixed_operator;     /* bal_mixed_operator: form of the FP32 copy of H (DIFFERENCE) */
 } bal_params;
 
 /* AL: Algorithm 1 (dual updates, sigma schedule, A' rule). PLAIN: the plain

@@ -19,6 +19,7 @@ OK = 0
 STATUS = {0: "OK", 1: "ARG", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
           6: "CUDA", 7: "LINE_SEARCH", 8: "STATE"}
 PREC_FP64, PREC_MIXED, PREC_DF64, PREC_FP32 = 0, 1, 2, 3
+MIXED_OP_DIFFERENCE, MIXED_OP_PLAIN = 0, 1   # bal_mixed_operator values
 PRECOND_BJ, PRECOND_BJ_WARMSTART, PRECOND_ADDITIVE = 0, 1, 2
 STEP_CA, STEP_CCD = 0, 1
 BROAD_GRID, BROAD_LBVH = 0, 1
@@ -48,7 +49,7 @@ class Params(C.Structure):
                 ("al_mode", C.c_int32), ("pcg_tol_mode", C.c_int32),
                 ("friction", C.c_double), ("friction_eps_v", C.c_double),
                 ("spmv_window", C.c_int32), ("ls_extra_rounds", C.c_int32),
-                ("pcg_stall_forcing", C.c_double)]
+                ("pcg_stall_forcing", C.c_double), ("mixed_operator", C.c_int32)]
 
 
 class SceneDesc(C.Structure):

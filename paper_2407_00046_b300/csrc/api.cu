@@ -580,7 +580,8 @@ static bool params_ok(const bal_params* p) {
       !(p->step_bound > 0 && p->step_bound < 1) || !(p->sigma_growth >= 1) ||
       !(p->friction >= 0) || !(p->friction_eps_v >= 0) ||
       p->spmv_window < 0 || p->spmv_window > 4096 || (p->spmv_window % 32) != 0 ||
-      p->ls_extra_rounds < 0 || !(p->pcg_stall_forcing >= 0));
+      p->ls_extra_rounds < 0 || !(p->pcg_stall_forcing >= 0) ||
+      p->mixed_operator < BAL_MIXED_OP_DIFFERENCE || p->mixed_operator > BAL_MIXED_OP_PLAIN);
 }
 
 void bal_default_params(bal_params* p) {
@@ -605,9 +606,9 @@ void bal_default_params(bal_params* p) {
   p->ls_extra_pcg = 100;
   p->warm_tol = 1e-2;
   p->warm_max_iter = 50;
-  p->mixed_inner_max = 200;
-  p->mixed_inner_tol = 1e-3;
-  p->mixed_max_refine = 20;
+  p->mixed_inner_max = 3000;
+  p->mixed_inner_tol = 1e-2;
+  p->mixed_max_refine = 40;
   p->ca_max_iter = 64;
   p->freeze_al = 0;
   p->step_mode = BAL_STEP_CA;
@@ -619,6 +620,7 @@ void bal_default_params(bal_params* p) {
   p->spmv_window = 0;
   p->ls_extra_rounds = 10;
   p->pcg_stall_forcing = 0.0;
+  p->mixed_operator = BAL_MIXED_OP_DIFFERENCE;
 }
 
 bal_status bal_create_scene(const bal_scene_desc* desc, const bal_params* params, bal_scene** out) {
@@ -875,7 +877,7 @@ bal_status bal_destroy_scene(bal_scene* sc) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t& e : S.kaev)
     if (e) cudaEventDestroy(e);
-  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.emit_keys, &S.emit_vals, &S.cm_cnt,
+  Buf* bufs[] = {&S.C_row, &S.C_col, &S.C_val, &S.C_val32, &S.f32_S, &S.emit_keys, &S.emit_vals, &S.cm_cnt,
                  &S.cm_off, &S.cm_bucket, &S.cm_sorted, &S.cm_ucnt, &S.cm_uoff, &S.scan_aux, &S.cub_tmp, &S.bp_cells,
                  &S.bp_cells_alt, &S.bp_ids, &S.bp_ids_alt, &S.bp_count, &S.bp_offs, &S.cand,
                  &S.cand_alt, &S.dist, &S.dist_alt, &S.flags, &S.eval_keys, &S.eval_flags, &S.eval_mu, &S.eval_s,

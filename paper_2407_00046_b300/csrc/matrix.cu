@@ -116,6 +116,10 @@ struct OffDiag {
   const T* Cval;
   int64_t nC;
   const int32_t* group;   // non-null: skip blocks whose row and column groups differ (Sec. 4.2.1)
+  // 1: difference form -- block (i, j) adds B (v_j - v_i) to row i and
+  // B^T (v_i - v_j) to row j, with the diagonal blocks of the system holding
+  // m_i/h^2 I + S_i (see make_f32_copy) instead of D_i
+  int diff = 0;
 };
 
 // A symmetric block system: diagonal blocks, their inverses, off-diagonal blocks.
@@ -156,8 +160,14 @@ __global__ void k_spmv_offdiag(OffDiag<T> O, const T* __restrict__ v, T* __restr
     const T* B;
     block_of(O, b, i, j, B);
     if (O.group && O.group[i] != O.group[j]) continue;
-    atomic_addv(y, i, mv(B, ldv(v, j)));
-    atomic_addv(y, j, mtv(B, ldv(v, i)));
+    if (O.diff) {
+      const V3<T> d = axpyv(T(-1), ldv(v, i), ldv(v, j));   // v_j - v_i
+      atomic_addv(y, i, mv(B, d));
+      atomic_addv(y, j, axpyv(T(-1), mtv(B, d), V3<T>{T(0), T(0), T(0)}));
+    } else {
+      atomic_addv(y, i, mv(B, ldv(v, j)));
+      atomic_addv(y, j, mtv(B, ldv(v, i)));
+    }
   }
 }
 
@@ -269,10 +279,18 @@ __global__ void __launch_bounds__(NT) k_pcg_offdiag(OffDiag<T> O, const T* __res
     block_of(O, b, i, j, B);
     if (O.group && O.group[i] != O.group[j]) continue;
     const V3<T> pj = ldv(p, j), pi = ldv(p, i);
-    const V3<T> bpj = mv(B, pj);
-    atomic_addv(q, i, bpj);
-    atomic_addv(q, j, mtv(B, pi));
-    plp += 2.0 * (double)dotv(pi, bpj);
+    if (O.diff) {
+      const V3<T> d = axpyv(T(-1), pi, pj);   // p_j - p_i
+      const V3<T> bd = mv(B, d), btd = mtv(B, d);
+      atomic_addv(q, i, bd);
+      atomic_addv(q, j, axpyv(T(-1), btd, V3<T>{T(0), T(0), T(0)}));
+      plp += (double)dotv(pi, bd) - (double)dotv(pj, btd);
+    } else {
+      const V3<T> bpj = mv(B, pj);
+      atomic_addv(q, i, bpj);
+      atomic_addv(q, j, mtv(B, pi));
+      plp += 2.0 * (double)dotv(pi, bpj);
+    }
   }
   plp = block_sum<double, NT>(plp);
   if (threadIdx.x == 0) partials[n_prev + blockIdx.x] = plp;
@@ -353,6 +371,34 @@ __global__ void k_groups(const double* __restrict__ lam, int nv, int32_t* __rest
   }
 }
 
+// Difference form of the FP32 copy. Every stencil Hessian of H except the
+// mass term is translation invariant (elastic energies and contact distances
+// depend on position differences only), so the blocks of a row sum to
+// m_i/h^2 I, apart from rows that lost blocks to pinned neighbours. Writing
+//   (H v)_i = G_i v_i + sum_j B_ij (v_j - v_i),  G_i = D_i + sum_j B_ij
+// (sum over row i's off-diagonal blocks, L, C and their transposes), with G_i
+// summed in FP64 before its single rounding (it equals m_i/h^2 I to FP64
+// rounding in the interior), keeps that invariance exact in FP32: rounding the
+// stiff blocks perturbs H v by eps |B| |v_j - v_i| instead of eps |D| |v|, so
+// the smooth, near-rigid modes that carry the smallest eigenvalues of a stiff
+// body (and the large condition number) keep their FP32 operator close to H's.
+__global__ void k_diffdiag_rows(OffDiag<double> O, double* __restrict__ G) {
+  const int64_t n = O.nL + O.nC;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int i, j;
+    const double* B;
+    block_of(O, b, i, j, B);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        atomicAdd(G + 9 * (int64_t)i + 3 * r + c, B[3 * r + c]);   // B in row i
+        atomicAdd(G + 9 * (int64_t)j + 3 * r + c, B[3 * c + r]);   // B^T in row j
+      }
+  }
+}
+
 template <typename T>
 __global__ void k_convert(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -364,6 +410,16 @@ __global__ void k_refine_update(int64_t n, double s, const float* __restrict__ e
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] += s * (double)e[i];
+}
+// partial sums of e . r (FP32 e, FP64 r) in FP64
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dot_fd(int64_t n, const float* __restrict__ e,
+                                               const double* __restrict__ r, double* partials) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+    acc += (double)e[i] * r[i];
+  acc = block_sum<double, NT>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 // r32 = (float)(r * s)
 __global__ void k_scale_to_f32(int64_t n, double s, const double* __restrict__ r, float* __restrict__ o) {
@@ -392,7 +448,8 @@ Sys<float> sys32(Scene& S) {
   A.D = S.D32;
   A.Dinv = S.Dinv32;
   A.O = OffDiag<float>{S.d.L_row, S.d.L_col, S.Lval32, S.d.nnzL, S.C_row.as<int32_t>(),
-                       S.C_col.as<int32_t>(), S.C_val32.as<float>(), S.nnzC, nullptr};
+                       S.C_col.as<int32_t>(), S.C_val32.as<float>(), S.nnzC, nullptr,
+                       S.f32_form == BAL_MIXED_OP_DIFFERENCE ? 1 : 0};
   A.nv = S.d.nv;
   return A;
 }
@@ -686,8 +743,22 @@ bal_status launch_dinv(Scene& S, cudaStream_t st) {
 
 bal_status make_f32_copy(Scene& S, cudaStream_t st) {
   const int64_t n9 = 9 * (int64_t)S.d.nv;
-  k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.D, S.D32);
-  ::bal::note_launch();
+  if (S.prm.mixed_operator == BAL_MIXED_OP_DIFFERENCE) {
+    BAL_TRY(buf_reserve(S.f32_S, sizeof(double) * n9));
+    double* G = S.f32_S.as<double>();
+    BAL_CUDA(cudaMemcpyAsync(G, S.d.D, sizeof(double) * n9, cudaMemcpyDeviceToDevice, st));
+    const Sys<double> A = sys64(S);
+    if (A.O.nL + A.O.nC > 0) {
+      k_diffdiag_rows<<<grid_for(A.O.nL + A.O.nC, kThreads, kNumSM * 16), kThreads, 0, st>>>(A.O, G);
+      ::bal::note_launch();
+    }
+    k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, G, S.D32);
+    ::bal::note_launch();
+  } else {
+    k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.D, S.D32);
+    ::bal::note_launch();
+  }
+  S.f32_form = S.prm.mixed_operator;
   k_convert<float><<<grid_for(n9), kThreads, 0, st>>>(n9, S.d.Dinv, S.Dinv32);
   ::bal::note_launch();
   if (S.d.nnzL) {
@@ -740,32 +811,31 @@ bal_status residual_fp64(Scene& S, const double* b, const double* x, double* r, 
   return BAL_OK;
 }
 
-// FP64 value of the quadratic model f(x) = x^T H x / 2 - b^T x from x and its
-// residual r = b - H x: f = -(b.x + r.x) / 2. f(x) - f(x*) = |x - x*|_H^2 / 2, so
-// f falls exactly when the error falls in the energy norm, the norm CG reduces.
-static bal_status quad_model(Scene& S, int64_t n3, const double* b, const double* r, const double* x,
-                             double* f, cudaStream_t st) {
-  BAL_TRY(launch_dot(S, n3, b, x, 30, st));
-  BAL_TRY(launch_dot(S, n3, r, x, 31, st));
-  double v[2];
-  BAL_CUDA(cudaMemcpyAsync(v, S.scal + 30, sizeof(v), cudaMemcpyDeviceToHost, st));
+// e . r in FP64 for the FP32 correction e and an FP64 residual r (host value)
+static bal_status dot_fd(Scene& S, int64_t n3, const float* e, const double* r, double* out, cudaStream_t st) {
+  k_dot_fd<kRedThreads><<<kRedBlocks, kRedThreads, 0, st>>>(n3, e, r, S.partials);
+  ::bal::note_launch();
+  BAL_LAUNCH_CHECK();
+  BAL_TRY(finish_reduce(S, kRedBlocks, 30, RED_SUM, st));
+  BAL_CUDA(cudaMemcpyAsync(out, S.scal + 30, sizeof(double), cudaMemcpyDeviceToHost, st));
   BAL_CUDA(cudaStreamSynchronize(st));
-  *f = -0.5 * (v[0] + v[1]);
   return BAL_OK;
 }
 
 // FP32 inner PCG on the FP32 copy of H, FP64 outer residual and correction
 // (iterative refinement): r = b - H x (FP64), solve H e = r/||r|| in FP32 to
-// mixed_inner_tol, trial x + ||r|| e, repeat until ||r|| <= tol ||r_0||.
-// A pass is kept if it lowers the FP64 quadratic model (the energy-norm
-// error, which CG reduces monotonically even while ||r||_2 rises) or the FP64
-// residual (near convergence the model's decrease, ~||e||_H^2, is below the
-// rounding of f itself); a pass that lowers neither is rolled back and ends
-// the solve. On exit without convergence x is the iterate with the smallest
-// FP64 residual seen.
+// mixed_inner_tol, trial x + d with d = ||r|| e, repeat until ||r|| <= tol
+// ||r_0||. A pass is kept if it lowers the FP64 quadratic model f(x) =
+// x^T H x / 2 - b^T x -- the energy-norm error, which CG reduces
+// monotonically even while ||r||_2 rises -- or the FP64 residual. The change
+// of f is formed from the correction and the two residuals,
+// f(x + d) - f(x) = -d.(r + r_new) / 2 (r_new = r - H d), so it carries no
+// cancellation against f itself and stays meaningful down to the tolerance.
+// A pass that lowers neither is rolled back and ends the solve. On exit
+// without convergence x is the iterate with the smallest FP64 residual seen.
 static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, int max_it,
                             bal_solve_info* info, cudaStream_t st) {
-  if (!S.f32_valid) {
+  if (!S.f32_valid || S.f32_form != S.prm.mixed_operator) {
     BAL_TRY(make_f32_copy(S, st));
     S.f32_valid = true;
   }
@@ -775,8 +845,6 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
   double rn, bn;
   BAL_TRY(residual_fp64(S, b, x, S.pcg_r, &rn, &bn, st));
   const double r0 = rn;
-  double fx;
-  BAL_TRY(quad_model(S, n3, b, S.pcg_r, x, &fx, st));
   double best_rn = rn;
   bool best_is_x = true;
   int total = 0, passes = 0;
@@ -799,6 +867,8 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
     total += h.it;
     passes += 1;
     if (h.it == 0) break;
+    double er, er_new;   // e . r before and after the pass (d = rn e)
+    BAL_TRY(dot_fd(S, n3, S.x32, S.pcg_r, &er, st));
     BAL_CUDA(cudaMemcpyAsync(xtrial, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
     k_refine_update<<<grid_for(n3), kThreads, 0, st>>>(n3, rn, S.x32, xtrial);
     ::bal::note_launch();
@@ -809,9 +879,9 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
       set_error("mixed pcg: non-finite residual after refinement pass %d", passes);
       return BAL_ERR_NAN;
     }
-    double f_new;
-    BAL_TRY(quad_model(S, n3, b, S.pcg_r, xtrial, &f_new, st));
-    if (!(f_new < fx) && !(rn_new < rn)) {
+    BAL_TRY(dot_fd(S, n3, S.x32, S.pcg_r, &er_new, st));
+    const double df = -0.5 * rn * (er + er_new);   // f(x + d) - f(x)
+    if (!(df < 0.0) && !(rn_new < rn)) {
       // neither the energy-norm error (f) nor the FP64 residual fell: roll the
       // pass back (x and its residual norm stay those of the previous pass;
       // S.pcg_r is not used after the loop)
@@ -822,7 +892,6 @@ static bal_status pcg_mixed(Scene& S, const double* b, double* x, double tol, in
       best_is_x = false;
     }
     BAL_CUDA(cudaMemcpyAsync(x, xtrial, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-    fx = f_new;
     rn = rn_new;
     if (rn <= best_rn) {
       best_rn = rn;

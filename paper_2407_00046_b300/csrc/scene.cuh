@@ -82,6 +82,8 @@ struct Scene {
   float *D32 = nullptr, *Dinv32 = nullptr, *Lval32 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
   bool f32_valid = false;
+  int32_t f32_form = -1;         // bal_mixed_operator the FP32 copy was built in
+  Buf f32_S;                     // FP64 sums of the difference form's diagonal blocks [nv][9]
   Buf add_inv;                   // additive preconditioner: inverses of the 27x27 group blocks
   // BAL_PREC_DF64 solve (ddpcg.cu). The static lower blocks in a symmetric
   // sliced-ELL layout of 32-row slices, built on first use: per slice the

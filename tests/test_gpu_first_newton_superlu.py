@@ -17,10 +17,11 @@ What is checked, per solver form:
   ||p - p_LU||_2 <= (||b - H p|| + ||r_LU||) / lambda_lb; this bounds the
   largest per-vertex difference too.
 
-The FP32 + FP64-refinement form is held to the same bound when it reports
-convergence; otherwise (kappa of the 1e9 cubes against the FP32 epsilon) it
-must at least return a direction whose residual is no larger than ||b||
-(a refinement pass that raises the FP64 residual is rolled back)."""
+The FP32 + FP64-refinement form (FP32 operator in difference form) is held to
+the same bound when it reports convergence; otherwise (kappa of the 1e9 cubes
+against the FP32 epsilon) it must at least return a direction whose residual
+is no larger than ||b|| (a refinement pass that raises the FP64 residual is
+rolled back)."""
 import time
 
 import numpy as np
@@ -36,10 +37,11 @@ from paper_2407_00046_b300 import bal, scenes  # noqa: E402
 TOL = 1e-6
 # Block-Jacobi leaves the rigid modes of the free 1e9 Pa cubes at eigenvalues
 # (m_v / h^2) / K_diag ~ 4e-8 of D^-1 H, so kappa ~ 5e7 and CG needs on the
-# order of sqrt(kappa) ln(2 / tol) ~ 1e5 iterations; the FP32 inner solves of
-# the mixed form cannot resolve those modes (kappa * eps_32 ~ 3), so its cap
-# only bounds the test's time.
-MAX_ITER = {"fp64": 200000, "df64": 200000, "mixed": 30000}
+# order of sqrt(kappa) ln(2 / tol) ~ 1e5 iterations; the mixed form restarts
+# CG on every refinement pass, and rounding to FP32 still moves the rotation
+# modes by ~kappa eps_32 |edge| / |body| relative, so its cap only bounds the
+# test's time.
+MAX_ITER = {"fp64": 200000, "df64": 200000, "mixed": 100000}
 
 
 @pytest.fixture(scope="module")
@@ -80,8 +82,8 @@ def test_first_newton_direction_matches_superlu(oracle_system, gpu_scene, form):
     sc, e, H, p_lu, r_lu, lam_lb = oracle_system
     S, g = gpu_scene
     prec = {"fp64": bal.PREC_FP64, "df64": bal.PREC_DF64, "mixed": bal.PREC_MIXED}[form]
-    S.set_params(precision=prec, pcg_stall_window=20000, pcg_max_iter=MAX_ITER[form], mixed_inner_max=1000,
-                 mixed_max_refine=40, mixed_inner_tol=1e-3)
+    S.set_params(precision=prec, pcg_stall_window=20000, pcg_max_iter=MAX_ITER[form], mixed_inner_max=3000,
+                 mixed_max_refine=60, mixed_inner_tol=1e-2)
     sol = torch.zeros_like(g)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
