@@ -1043,19 +1043,44 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
   PcgScalars h;
   BAL_TRY(pcg_core<double>(S, sys64(S), b, S.pcg_q, x, S.pcg_r, S.pcg_z, S.pcg_p, S.pcg_q, tol,
                            max_it, S.prm.pcg_stall_window, &h, st));
+  // On a very ill-conditioned system the recursive residual of FP64 CG drifts
+  // from b - H x (the gap reaches a few tolerances at kappa ~ 1e8). When the
+  // recursion reports convergence, the FP64 residual decides: CG restarts from
+  // it while it is above tol ||r_0|| (at most mixed_max_refine restarts, within
+  // max_it iterations in total); a restart that does not lower the FP64
+  // residual by 1% (the rounding floor of H x) ends the solve unconverged.
+  const double r0 = h.r0norm;
+  int total = h.it, restarts = 0;
+  bool converged = h.converged != 0, stagnated = h.stagnated != 0, have_true = false;
+  double rn = 0.0, bn = 0.0, prev = INFINITY;
+  while (converged) {
+    BAL_TRY(true_residual(S, b, x, &rn, &bn, st));   // leaves H x in S.pcg_q
+    have_true = true;
+    if (rn <= tol * r0 || restarts >= S.prm.mixed_max_refine || total >= max_it || !(rn < 0.99 * prev)) {
+      converged = rn <= tol * r0;
+      break;
+    }
+    prev = rn;
+    ++restarts;
+    BAL_TRY(pcg_core<double>(S, sys64(S), b, S.pcg_q, x, S.pcg_r, S.pcg_z, S.pcg_p, S.pcg_q, tol * r0 / rn,
+                             max_it - total, S.prm.pcg_stall_window, &h, st));
+    total += h.it;
+    converged = h.converged != 0;
+    stagnated = h.stagnated != 0;
+    have_true = false;
+  }
   if (info) {
-    info->iters = h.it;
-    info->stagnated = h.stagnated;
-    info->converged = h.converged;
-    info->refine_passes = 0;
+    info->iters = total;
+    info->stagnated = stagnated ? 1 : 0;
+    info->converged = converged ? 1 : 0;
+    info->refine_passes = restarts;
     info->warm_iters = witers;
     info->n_groups = ngroups;
     info->negative_curvature = 0;
     info->precision_used = BAL_PREC_FP64;
-    double rn, bn;
-    BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
+    if (!have_true) BAL_TRY(true_residual(S, b, x, &rn, &bn, st));
     info->rel_residual = bn > 0 ? rn / bn : rn;
-    info->rel_residual_r0 = h.r0norm > 0 ? rn / h.r0norm : rn;
+    info->rel_residual_r0 = r0 > 0 ? rn / r0 : rn;
   }
   return BAL_OK;
 }
