@@ -415,6 +415,38 @@ def run_precision_sweep(args):
             "data": "synthetic (seeded procedural scene)"}
 
 
+def budgeted_time_step(S, x, v, stream, budget_s):
+    """One time step through the public calls -- bal_step_begin, Algorithm 1
+    iterations (bal_newton_step) until the convergence test, the Newton cap or
+    the wall-clock budget, bal_step_end -- with the bal_time_step summary."""
+    t0 = time.perf_counter()
+    S.step_begin(x, v, stream=stream)
+    out = {"newton_iters": 0, "pcg_iters_total": 0, "converged": 0, "max_active": 0,
+           "min_distance": float("inf"), "ms_assemble": 0.0, "ms_solve": 0.0, "ms_line_search": 0.0,
+           "ms_contact": 0.0, "status": 3, "budget_hit": 0}       # 3: BAL_ERR_NOT_CONVERGED
+    out["sigma0"] = S.get_al_state()["sigma0"]
+    for _ in range(S.get_params().newton_max_iter):
+        ni = S.newton_step(x, stream=stream, check=False)
+        for kk in ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact"):
+            out[kk] += ni[kk]
+        out["pcg_iters_total"] += ni["pcg_iters"]
+        out["max_active"] = max(out["max_active"], ni["n_active"])
+        out["min_distance"] = min(out["min_distance"], ni["dmin"])
+        if ni["status"] != 0:
+            out["status"] = ni["status"]
+            break
+        if ni["converged"]:
+            out["status"], out["converged"] = 0, 1
+            break
+        out["newton_iters"] += 1
+        if time.perf_counter() - t0 > budget_s:
+            out["budget_hit"] = 1
+            break
+    out["sigma_final"] = S.get_al_state()["sigma"]
+    S.step_end(x, v, stream=stream)
+    return out
+
+
 def reduce_over_ranks(ms, e2e_ms, pcg_iters, e2e_iters, world, dev=None):
     """Whole-job figures of a replicas-only run: the slowest rank's times (max)
     and the PCG iterations of all ranks (sum). One collective per figure kind,
@@ -466,12 +498,18 @@ def run_ours(args, rank, world):
               f"{info['ms_solve']:.0f} ls {info['ms_line_search']:.0f} contact {info['ms_contact']:.0f})",
               file=sys.stderr, flush=True)
 
-    # 1. whole time steps to convergence (Newton cap --newton-max), one by one
+    # 1. whole time steps to convergence (Newton cap --newton-max), one by one,
+    # within a wall-clock budget for the phase (a step still open when it runs
+    # out ends unconverged, like one at the Newton cap, and no further step starts)
     time_steps = []
+    t_phase = time.perf_counter()
     for k in range(args.time_steps):
+        left = args.time_step_budget - (time.perf_counter() - t_phase)
+        if left <= 0:
+            break
         e0, e1 = _events()
         e0.record(stream)
-        info = S.time_step(x, v, stream=stream, check=False)
+        info = budgeted_time_step(S, x, v, stream, left)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -480,7 +518,7 @@ def run_ours(args, rank, world):
                            "ms": round(ms, 1), "newton_iters": info["newton_iters"],
                            "pcg_iters": info["pcg_iters_total"], "max_active": info["max_active"],
                            "min_distance": info["min_distance"], "sigma0": info["sigma0"],
-                           "sigma_final": info["sigma_final"],
+                           "sigma_final": info["sigma_final"], "budget_hit": info["budget_hit"],
                            "phase_ms": {kk: round(info[kk], 1) for kk in
                                         ("ms_assemble", "ms_solve", "ms_line_search", "ms_contact")}})
 
@@ -607,10 +645,12 @@ def run_ours(args, rank, world):
             "converged": f"{sum(t['converged'] for t in time_steps)}/{len(time_steps)}",
             "capped_ms": [t["ms"] for t in contact_steps if not t["converged"]],
             "note": "each time step from the initial state run to convergence (Alg. 1 test "
-                    "||e||/||e0|| <= newton_tol) or the Newton cap, timed with CUDA events; "
-                    "ms_per_time_step and newton_iters_per_time_step are the means over the "
-                    "steps in contact that converged (null if none did); capped_ms lists the "
-                    "contact steps that reached the cap",
+                    "||e||/||e0|| <= newton_tol), the Newton cap or the phase's wall-clock "
+                    "budget (budget_hit), timed with CUDA events; ms_per_time_step and "
+                    "newton_iters_per_time_step are the means over the steps in contact that "
+                    "converged (null if none did); capped_ms lists the contact steps that "
+                    "did not converge",
+            "budget_s": args.time_step_budget,
             "steps": time_steps,
         },
         "alg1_iterations": {
@@ -809,6 +849,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10,
                     help="timed bench steps: Algorithm 1 iterations (one pass of the hot path each)")
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--time-step-budget", type=float, default=540.0,
+                    help="wall-clock seconds for the --time-steps phase (keeps the default run bounded)")
     ap.add_argument("--time-steps", type=int, default=3,
                     help="time steps run to convergence and timed one by one before the bench steps "
                          "(free fall, impact, first step in contact on the default workload)")

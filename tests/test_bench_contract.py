@@ -1,6 +1,7 @@
 """The benchmark's measurement contract on CPU: the dominant kernel's
 algorithmic bytes, the roofline fraction, the DRAM-traffic record and its
-source-hash guard, the measured peak, and the defaults of a run."""
+source-hash guard, the measured peak, the defaults of a run, and the
+time-step phase's summary and wall-clock budget (on a host stand-in scene)."""
 import json
 import os
 import sys
@@ -65,3 +66,52 @@ def test_default_run_is_one_gpu_a_few_steps():
     assert d["gpus"] == 1 and d["warmup"] >= 3 and 1 <= d["steps"] <= 20
     assert d["sigma_rule"] == "printed" and d["newton_max"] >= 200 and d["time_steps"] >= 2
     assert d["scene"] == "chain_net_shells" and d["precision"] == "df64"
+
+
+class _FakeScene:
+    """Host stand-in for a scene: Algorithm 1 converges at iteration `conv`."""
+
+    def __init__(self, conv, sleep=0.0):
+        self.conv, self.sleep, self.calls, self.ended = conv, sleep, 0, False
+
+    def step_begin(self, x, v, stream=None):
+        self.calls = 0
+
+    def step_end(self, x, v, stream=None):
+        self.ended = True
+
+    def get_al_state(self):
+        return {"sigma": 2.0 * (1 + self.calls), "sigma0": 2.0}
+
+    def get_params(self):
+        class P:
+            newton_max_iter = 50
+        return P()
+
+    def newton_step(self, x, stream=None, check=True):
+        import time
+        time.sleep(self.sleep)
+        self.calls += 1
+        return {"status": 0, "converged": int(self.calls > self.conv), "pcg_iters": 10, "n_active": self.calls,
+                "dmin": 1.0 / self.calls, "ms_assemble": 1.0, "ms_solve": 2.0, "ms_line_search": 0.5,
+                "ms_contact": 0.25}
+
+
+def test_budgeted_time_step_matches_the_time_step_summary():
+    S = _FakeScene(conv=4)
+    out = bench.budgeted_time_step(S, None, None, None, budget_s=1e9)
+    # four iterations that do not pass the test, then the one that does
+    assert out["converged"] == 1 and out["status"] == 0 and out["newton_iters"] == 4
+    assert out["pcg_iters_total"] == 50 and out["max_active"] == 5 and out["min_distance"] == 0.2
+    assert out["ms_solve"] == 10.0 and out["sigma0"] == 2.0 and out["sigma_final"] == 12.0
+    assert S.ended and out["budget_hit"] == 0
+
+
+def test_budgeted_time_step_stops_at_the_budget_and_the_cap():
+    S = _FakeScene(conv=10 ** 6, sleep=0.02)
+    out = bench.budgeted_time_step(S, None, None, None, budget_s=0.05)
+    assert out["budget_hit"] == 1 and out["converged"] == 0 and out["status"] == 3
+    assert 1 <= out["newton_iters"] < 50 and S.ended
+    S = _FakeScene(conv=10 ** 6)
+    out = bench.budgeted_time_step(S, None, None, None, budget_s=1e9)
+    assert out["newton_iters"] == 50 and out["converged"] == 0 and out["budget_hit"] == 0
