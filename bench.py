@@ -137,6 +137,29 @@ def spmv_kernel_bytes(precision, nv, nnzL, nnzC):
     return "k_pcg_offdiag (symmetric off-diagonal blocks, atomics)", nb * (9 * p + 8) + 3 * 3 * nv * p
 
 
+def pcg_iteration_bytes(nv, nnzL, nnzC):
+    """Method-minimal bytes of one block-Jacobi PCG iteration with 8-byte
+    values (FP64 or double-float): the symmetric SpMV (matrix read once, p
+    read, q written) plus the vector work fused into two passes -- x += alpha p,
+    r -= alpha q, z = D^-1 r (read x, p, q, r and D^-1; write x, r, z) and
+    p = z + beta p (read z, p; write p): 24 B per vertex per vector access,
+    72 B per D^-1 block, 312 B per vertex in all."""
+    _, spmv = spmv_kernel_bytes("df64", nv, nnzL, nnzC)
+    return spmv + (7 * 24 + 72 + 3 * 24) * nv
+
+
+def pcg_iteration_roofline(precision, nv, nnzL, nnzC, iters_per_s, peak, peak_kind):
+    """The whole PCG iteration against the measured HBM bandwidth: its
+    method-minimal bytes at the PCG-only iteration rate (8-byte-value forms)."""
+    if precision not in ("df64", "fp64") or not iters_per_s:
+        return None
+    byts = pcg_iteration_bytes(nv, nnzL, nnzC)
+    gbs = byts * iters_per_s / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "bytes_per_iteration": byts, "iters_per_s": round(iters_per_s, 1),
+            "achieved": round(gbs, 1), "peak": peak, "peak_kind": peak_kind, "frac": round(gbs / peak, 4),
+            "note": "SpMV, update and direction kernels of one iteration; the rate is pcg_only_iters_per_s"}
+
+
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture on the chain-net workload (profiles/k_dd_spmv_chain_net_shells.md),
 # valid while the kernel's sources hash to the values recorded with it.
@@ -259,7 +282,10 @@ def run_pcg_only(args):
             "iters_per_s": round(1e3 / ms, 1), "nnz_L": view["nnz_L"], "nnz_C": view["nnz_C"],
             "warm_steps": warm_steps, "n_verts": sc.n_verts,
             "spmv_kernel": kname, "spmv_ms_per_launch": round(kms, 5),
-            "spmv_gbs": round(byts / (kms * 1e-3) / 1e9, 1), "spmv_bytes": byts}
+            "spmv_gbs": round(byts / (kms * 1e-3) / 1e9, 1), "spmv_bytes": byts,
+            "pcg_iteration_bytes": pcg_iteration_bytes(sc.n_verts, view["nnz_L"], view["nnz_C"]),
+            "pcg_iteration_gbs": round(pcg_iteration_bytes(sc.n_verts, view["nnz_L"], view["nnz_C"])
+                                       / (ms * 1e-3) / 1e9, 1)}
 
 
 def _scene_params(args, bal, **kw):
@@ -666,6 +692,8 @@ def run_ours(args, rank, world):
         },
         "max_active_pairs": max([t["max_active"] for t in time_steps] + [t["n_active"] for t in timed]),
         "pcg_only_iters_per_s": round(pcg_only, 1),
+        "roofline_pcg_iteration": pcg_iteration_roofline(args.precision, nv, nnzL, nnzC, pcg_only, peak,
+                                                         peak_kind),
         "e2e": {"value": round(e2e_val, 2), "unit": "PCG iter/s",
                 "h2d_bytes_per_step": 3 * nv * 8, "d2h_bytes_per_step": 3 * nv * 8},
         "roofline": roofline_entry(args.precision, kname, achieved, peak, peak_kind, byts, spmv_ms,

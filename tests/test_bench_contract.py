@@ -115,3 +115,14 @@ def test_budgeted_time_step_stops_at_the_budget_and_the_cap():
     S = _FakeScene(conv=10 ** 6)
     out = bench.budgeted_time_step(S, None, None, None, budget_s=1e9)
     assert out["newton_iters"] == 50 and out["converged"] == 0 and out["budget_hit"] == 0
+
+
+def test_pcg_iteration_bytes_are_the_spmv_plus_two_fused_vector_passes():
+    nv, nL, nC = 433336, 2454448, 0
+    _, spmv = bench.spmv_kernel_bytes("df64", nv, nL, nC)
+    b = bench.pcg_iteration_bytes(nv, nL, nC)
+    assert b - spmv == 312 * nv                   # 7 vector accesses + D^-1, then z, p read and p written
+    assert 375e6 < b < 376e6                      # the chain net's 1.77M-tet system
+    e = bench.pcg_iteration_roofline("df64", nv, nL, nC, 9000.0, 6500.0, "measured")
+    assert e["frac"] == round(b * 9000.0 / 1e9 / 6500.0, 4) and e["bound"] == "hbm"
+    assert bench.pcg_iteration_roofline("mixed", nv, nL, nC, 9000.0, 6500.0, "measured") is None
