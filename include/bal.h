@@ -217,7 +217,7 @@ typedef struct {
   double rel_residual_r0;     /* ||b - H x|| / ||r_0|| */
   int32_t stagnated;          /* 1 if stopped by the stagnation window */
   int32_t converged;          /* 1 if the tolerance was met */
-  int32_t refine_passes;      /* mixed / df64 precision: FP64 refinement passes */
+  int32_t refine_passes;      /* mixed: FP64 refinement passes; FP64 / df64: restarts from the FP64 residual */
   int32_t warm_iters;         /* warm start: subdomain PCG iterations */
   int32_t n_groups;           /* warm start: stiffness groups */
   int32_t negative_curvature; /* adjoint: 1 if the unprojected H was indefinite and the
