@@ -389,7 +389,9 @@ BAL_API bal_status bal_time_step(bal_scene* scene, double* x_inout, double* v_in
  * application that owns all device memory, or a loop that forbids allocation
  * after start-up): block-Jacobi PCG with the stopping rules of bal_pcg_solve
  * under the default parameters (||r|| <= rel_tol ||r_0||, no new minimum of
- * the preconditioned residual sqrt(r^T z) in 100 iterations, or max_iter), on
+ * the preconditioned residual sqrt(r^T z) in 100 iterations, or max_iter)
+ * but without its restarts from the FP64 residual (info->rel_residual reports
+ * that residual; a caller needing it below rel_tol calls again from sol), on
  * a caller-provided symmetric block matrix
  * H = D + L + L^T in DEVICE memory -- D [n_verts][9] diagonal blocks, nnz lower
  * blocks (rows[nnz], cols[nnz] with rows > cols, vals[nnz][9] row-major) --
