@@ -896,8 +896,9 @@ def main():
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS))
     ap.add_argument("--pcg-tol", type=float, default=1e-6)
     ap.add_argument("--newton-tol", type=float, default=1e-4)
-    ap.add_argument("--newton-max", type=int, default=800,
-                    help="Algorithm 1 iterations per time step (cap; the step reports convergence)")
+    ap.add_argument("--newton-max", type=int, default=2000,
+                    help="Algorithm 1 iterations per time step (cap; the step reports convergence); "
+                         "the --time-steps phase is bounded by --time-step-budget as well")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the three-precision comparison")
     ap.add_argument("--precond", default="block-jacobi", choices=sorted(PRECONDS),
