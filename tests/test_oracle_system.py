@@ -1,5 +1,7 @@
 """Pins for the global objective, gradient, assembled Hessian, contact terms
 and the assembled stiffness Lambda."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -144,3 +146,44 @@ def test_lambda_is_the_mean_clamped_eigenvalue_of_every_stencil(close_cubes):
     add(nodes, Hc)
     add(fs.nodes, friction.terms(fs, xd)[2])
     assert np.abs(lam - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_block_rows_sum_to_the_mass_term_away_from_pins(close_cubes):
+    """Translation invariance of every projected stencil Hessian (elastic,
+    contact with A and A', friction): away from pinned vertices the 3x3
+    blocks of a row of H sum to m_i/h^2 I, the property the difference form
+    of the FP32 operator relies on; rows next to a pinned vertex differ by the
+    blocks dropped with it."""
+    sc, m, x = close_cubes
+    rng = np.random.default_rng(3)
+    xd = x + 2e-5 * rng.normal(size=x.shape) * (sc.pinned == 0)[:, None]
+    y = system.inertia_target(m, sc.X, sc.V0)
+    keys, d = bal.active_pairs(m, xd)
+    assert len(keys) > 4
+    Ap_mu = {keys[k]: 0.5 + k for k in range(0, len(keys), 3)}     # some pairs also in A'
+    ps = bal.make_pairset(m, xd, keys, Ap_mu, 3.0)
+    assert ps.inAp.any()
+    fric = bal.friction_set(m, xd, x, ps, 3.0, bal.Params(friction=0.3))
+    assert fric is not None
+    H = system.hessian(m, xd, y, ps, 3.0, fric=fric).toarray()
+    n = sc.n_verts
+    T = np.zeros((3 * n, 3))
+    for a in range(3):
+        T[a::3, a] = 1
+    rows = (H @ T).reshape(n, 3, 3)                  # block-row sums
+    pinned = sc.pinned == 1
+    # stencil adjacency from the same system with nothing pinned (pinning
+    # zeroes the blocks between a free and a pinned vertex)
+    sc_free = copy.deepcopy(sc)
+    sc_free.pinned[:] = 0
+    m_free = system.make_model(sc_free)
+    H_free = system.hessian(m_free, xd, y, ps, 3.0, fric=fric).toarray()
+    Hb = np.abs(H_free).reshape(n, 3, n, 3).max(axis=(1, 3))
+    near_pin = (Hb[:, pinned] > 0).any(axis=1) & ~pinned
+    interior = ~pinned & ~near_pin
+    expect = (m.mass / m.h ** 2)[:, None, None] * np.eye(3)[None]
+    assert interior.sum() > n // 4 and near_pin.any()
+    assert np.abs(rows[interior] - expect[interior]).max() < 1e-9 * np.abs(H).max()
+    # with nothing pinned every row sums to its mass term
+    rows_free = (H_free @ T).reshape(n, 3, 3)
+    assert np.abs(rows_free - expect).max() < 1e-9 * np.abs(H_free).max()
