@@ -1016,8 +1016,30 @@ bal_status pcg_solve(Scene& S, const double* b, double* x, double tol, int max_i
   if (S.prm.precond == BAL_PRECOND_BJ_WARMSTART)
     BAL_TRY(warm_start(S, b, x, &witers, &ngroups, st));
   if (S.prm.precond == BAL_PRECOND_ADDITIVE) {   // FP64 whatever the precision setting
-    BAL_TRY(pcg_additive(S, b, x, tol, max_it, info, st));
+    // as for block-Jacobi below: the FP64 residual decides, with restarts from
+    // it while the recursion has drifted below tolerance
+    bal_solve_info ai{};
+    BAL_TRY(pcg_additive(S, b, x, tol, max_it, &ai, st));
+    const double r0 = ai.rel_residual_r0 > 0 ? ai.rel_residual / ai.rel_residual_r0 : 0.0;   // ||r_0|| / ||b||
+    int total = ai.iters, restarts = 0;
+    double prev = INFINITY;
+    while (ai.converged && ai.rel_residual > tol * r0 && restarts < S.prm.mixed_max_refine && total < max_it &&
+           ai.rel_residual < 0.99 * prev) {
+      prev = ai.rel_residual;
+      ++restarts;
+      bal_solve_info bi{};
+      BAL_TRY(pcg_additive(S, b, x, tol * r0 / ai.rel_residual, max_it - total, &bi, st));
+      total += bi.iters;
+      ai.converged = bi.converged;
+      ai.stagnated = bi.stagnated;
+      ai.rel_residual = bi.rel_residual;
+    }
+    ai.converged = ai.converged && ai.rel_residual <= tol * r0;
     if (info) {
+      *info = ai;
+      info->iters = total;
+      info->refine_passes = restarts;
+      info->rel_residual_r0 = r0 > 0 ? ai.rel_residual / r0 : ai.rel_residual;
       info->warm_iters = 0;
       info->n_groups = 0;
     }
