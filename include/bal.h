@@ -344,8 +344,9 @@ BAL_API bal_status bal_spmv(bal_scene* scene, const double* v, double* y, void* 
  * warm-started by the stiffness-grouped subdomain solve (Sec. 4.2.2), or in
  * FP32 with FP64 iterative refinement, from sol_inout. Stops at
  * ||r_k|| <= rel_tol ||r_0||, when the residual reaches no new minimum in
- * pcg_stall_window iterations, or at max_iter. In the FP64 and DF64 forms the
- * FP64 residual b - H x decides convergence: when the recursion reports it but
+ * pcg_stall_window iterations, or at max_iter. In the FP64 (block-Jacobi or
+ * additive) and DF64 forms the FP64 residual b - H x decides convergence:
+ * when the recursion reports it but
  * the FP64 residual is still above rel_tol ||r_0||, CG restarts from the FP64
  * residual (at most mixed_max_refine times; info->refine_passes counts them). */
 BAL_API bal_status bal_pcg_solve(bal_scene* scene, const double* rhs, double* sol_inout,
