@@ -118,7 +118,8 @@ struct OffDiag {
   const int32_t* group;   // non-null: skip blocks whose row and column groups differ (Sec. 4.2.1)
   // 1: difference form -- block (i, j) adds B (v_j - v_i) to row i and
   // B^T (v_i - v_j) to row j, with the diagonal blocks of the system holding
-  // m_i/h^2 I + S_i (see make_f32_copy) instead of D_i
+  // G_i = D_i + the sum of row i's off-diagonal blocks (k_diffdiag_rows)
+  // instead of D_i
   int diff = 0;
 };
 
