@@ -38,8 +38,8 @@ TOL = 1e-6
 # Block-Jacobi leaves the rigid modes of the free 1e9 Pa cubes at eigenvalues
 # (m_v / h^2) / K_diag ~ 4e-8 of D^-1 H, so kappa ~ 5e7 and CG needs on the
 # order of sqrt(kappa) ln(2 / tol) ~ 1e5 iterations; the mixed form restarts
-# CG on every refinement pass, and rounding to FP32 still moves the rotation
-# modes by ~kappa eps_32 |edge| / |body| relative, so its cap only bounds the
+# CG on every refinement pass, and rounding the FP32 vectors still perturbs
+# the cubes' rotation modes by O(kappa eps_32), so its cap only bounds the
 # test's time.
 MAX_ITER = {"fp64": 200000, "df64": 200000, "mixed": 100000}
 
