@@ -63,7 +63,8 @@ typedef enum { BAL_PREC_FP64 = 0, BAL_PREC_MIXED = 1, BAL_PREC_DF64 = 2, BAL_PRE
  * G_i = D_i + the sum of row i's off-diagonal blocks summed in FP64 before its
  * one rounding (m_i/h^2 I wherever every block of the row is translation
  * invariant) -- the form stays exactly translation invariant in FP32, so
- * rounding the blocks of a stiff body barely moves its near-rigid modes.
+ * rounding the blocks of a stiff body leaves its translations exact (its
+ * rotations keep an error from rounding the FP32 vector itself).
  * PLAIN: D_i v_i + sum_j B_ij v_j with every block rounded to FP32. */
 typedef enum { BAL_MIXED_OP_DIFFERENCE = 0, BAL_MIXED_OP_PLAIN = 1 } bal_mixed_operator;
 /* BJ: block-Jacobi. BJ_WARMSTART: block-Jacobi after the stiffness-grouped

@@ -380,9 +380,11 @@ __global__ void k_groups(const double* __restrict__ lam, int nv, int32_t* __rest
 // (sum over row i's off-diagonal blocks, L, C and their transposes), with G_i
 // summed in FP64 before its single rounding (it equals m_i/h^2 I to FP64
 // rounding in the interior), keeps that invariance exact in FP32: rounding the
-// stiff blocks perturbs H v by eps |B| |v_j - v_i| instead of eps |D| |v|, so
-// the smooth, near-rigid modes that carry the smallest eigenvalues of a stiff
-// body (and the large condition number) keep their FP32 operator close to H's.
+// stiff blocks perturbs H v by eps |B| |v_j - v_i| instead of eps |D| |v|, so a
+// stiff body's translations, near-null modes of the elastic part that set a
+// large share of its condition number, keep their FP32 product equal to H's.
+// Its rotations improve less: rounding the FP32 vector itself perturbs each
+// vertex by eps |v_i|, which grows with the distance from the axis.
 __global__ void k_diffdiag_rows(OffDiag<double> O, double* __restrict__ G) {
   const int64_t n = O.nL + O.nC;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n;

@@ -8,9 +8,9 @@ D^-1 H are m_v / h^2 over the stiff diagonal -- the kappa that defeats FP32.
 Rounding every block of H to FP32 (the plain form) moves those modes by
 eps_32 |D| |v|; the difference form, (H v)_i = G_i v_i + sum_j B_ij (v_j - v_i)
 with G_i summed in FP64 before rounding, moves them by eps_32 |B| |v_j - v_i|
-only, because every stencil Hessian except the mass term is translation
-invariant (Sec. 3.1 objective: elastic energy and contact distances depend on
-position differences).
+only -- translations exactly not at all -- because every stencil Hessian
+except the mass term is translation invariant (Sec. 3.1 objective: elastic
+energy and contact distances depend on position differences).
 
 Checked: the difference form converges to the FP64 relative residual 1e-6 and
 its solution solves the ORACLE's assembled system (FP64, CPU) to that
