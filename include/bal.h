@@ -99,9 +99,10 @@ typedef struct {
   int32_t ls_extra_pcg;       /* App. B: extra PCG iterations when alpha < ls_min_alpha */
   double warm_tol;            /* warm-start subdomain PCG relative tolerance (1e-2) */
   int32_t warm_max_iter;      /* warm-start subdomain PCG iteration cap (50) */
-  int32_t mixed_inner_max;    /* FP32 inner PCG iterations per refinement pass */
-  double mixed_inner_tol;     /* FP32 inner relative tolerance per pass */
-  int32_t mixed_max_refine;   /* max FP64 refinement passes */
+  int32_t mixed_inner_max;    /* FP32 inner PCG iterations per refinement pass (3000) */
+  double mixed_inner_tol;     /* FP32 inner relative tolerance per pass (1e-2) */
+  int32_t mixed_max_refine;   /* max FP64 refinement passes, and max restarts from the FP64
+                                 residual of the FP64 / DF64 solves (40) */
   int32_t ca_max_iter;        /* step bound: conservative-advancement iterations per pair (64) */
   int32_t freeze_al;          /* 1: hold sigma, A', mu fixed (no dual update, no sigma schedule,
                                  no A' rule) -- the map the adjoint differentiates */
